@@ -1,0 +1,68 @@
+"""Checks of the synthetic input generators (no GPU needed)."""
+from __future__ import annotations
+
+import numpy as np
+
+import gen
+from gen import workloads
+
+
+def test_splitmix64_published_values():
+    # first outputs of SplitMix64 seeded with 0 (Steele, Lea & Flood 2014; Vigna's C reference)
+    assert [gen.splitmix64_at(0, k) for k in (1, 2, 3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_permutation_is_uniform_and_deterministic():
+    p = gen.permutation(1000, 7)
+    assert np.array_equal(np.sort(p), np.arange(1000))
+    assert np.array_equal(p, gen.permutation(1000, 7))
+    assert not np.array_equal(p, gen.permutation(1000, 8))
+    # position of element 0 over many seeds is roughly uniform over 4 buckets
+    pos = np.array([np.flatnonzero(gen.permutation(8, s) == 0)[0] for s in range(4000)])
+    counts = np.bincount(pos // 2, minlength=4)
+    assert (abs(counts - 1000) < 150).all()
+
+
+def test_list_random_structure():
+    succ, head, perm = gen.list_random(5000, 3, with_perm=True)
+    assert head == perm[0]
+    assert (succ == -1).sum() == 1
+    assert np.array_equal(succ[perm[:-1]], perm[1:])
+
+
+def test_er_range_and_determinism():
+    s, d = gen.er(1000, 100000, 1)
+    assert s.min() >= 0 and s.max() < 1000 and d.min() >= 0 and d.max() < 1000
+    s2, d2 = gen.er(1000, 100000, 1)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)
+    # endpoint counts are close to uniform
+    c = np.bincount(s, minlength=1000)
+    assert abs(c.mean() - 100) < 1e-9 and c.std() < 15
+
+
+def test_rmat_quadrant_probabilities():
+    scale, m = 10, 200000
+    src, dst = gen.rmat(scale, m, 0.57, 0.19, 0.19, 4)
+    assert src.min() >= 0 and src.max() < (1 << scale)
+    # degree skew: the heaviest vertex is far above the mean degree
+    deg = np.bincount(src, minlength=1 << scale) + np.bincount(dst, minlength=1 << scale)
+    assert deg.max() > 20 * deg.mean()
+
+
+def test_batch_generators():
+    sizes = workloads.batch_sizes(4096)
+    assert sizes.min() >= 256 and sizes.max() < (1 << 20)
+    succ, off, heads = gen.list_batch(np.array([3, 1, 5]), 1)
+    assert off.tolist() == [0, 3, 4, 9]
+    src, dst, eoff, voff = gen.er_batch(np.array([10, 4]), 2, 1, 1)
+    assert eoff.tolist() == [0, 20, 28] and voff.tolist() == [0, 10, 14]
+    assert src[:20].max() < 10 and src[20:].max() < 4
+
+
+def test_jobs_stream():
+    arr, kind, size = workloads.serve_jobs(20000, 0.001)
+    assert (np.diff(arr) > 0).all()
+    assert abs(np.diff(arr).mean() - 0.001) < 0.0001
+    assert abs((kind == 0).mean() - 0.7) < 0.02
+    assert size.min() >= 1024 and size.max() < (1 << 24)

@@ -1,0 +1,233 @@
+"""Pins for the CPU oracle: it is checked against what the definitions fix,
+never against itself or the CUDA path (no GPU needed)."""
+from __future__ import annotations
+
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gen import workloads
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out[key] = np.array([int(v) for v in vals], np.int64)
+    return out
+
+
+# ----------------------------------------------------------------- lists --
+
+def test_lr_golden():
+    g = _read_golden("lr_small.txt")
+    head = int(g["head"][0])
+    assert np.array_equal(oracle.lr_rank(g["succ"], head), g["rank"])
+    assert np.array_equal(oracle.lr_rank(g["succ_selfloop"], head), g["rank"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 100, 4096, 65537])
+@pytest.mark.parametrize("seed", [1, 17])
+def test_lr_closed_form(n, seed):
+    # the generator stores the k-th list element at perm[k], so rank[perm[k]] = n-1-k
+    succ, head, perm = gen.list_random(n, seed, with_perm=True)
+    rank = oracle.lr_rank(succ, head)
+    expect = np.empty(n, np.int32)
+    expect[perm] = np.arange(n - 1, -1, -1, dtype=np.int32)
+    assert np.array_equal(rank, expect)
+    pins.lr_invariants(succ, head, rank)
+
+
+def _distance_to_tail(succ, i):
+    d = 0
+    while succ[i] != -1 and succ[i] != i:
+        i = succ[i]
+        d += 1
+    return d
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7])
+def test_lr_brute_force_all_layouts(n):
+    # every storage layout of an n-element list; rank counted by following links
+    for order in itertools.permutations(range(n)):
+        succ = np.full(n, -1, np.int32)
+        for a, b in zip(order, order[1:]):
+            succ[a] = b
+        rank = oracle.lr_rank(succ, order[0])
+        expect = [_distance_to_tail(succ, i) for i in range(n)]
+        assert rank.tolist() == expect
+
+
+def test_lr_ordered_control():
+    succ, head = workloads.lr_ordered(12)
+    rank = oracle.lr_rank(succ, head)
+    assert np.array_equal(rank, np.arange((1 << 12) - 1, -1, -1))
+
+
+def test_lr_empty():
+    assert oracle.lr_rank(np.empty(0, np.int32), 0).shape == (0,)
+
+
+@pytest.mark.parametrize("succ,head", [
+    ([1, 0], 0),                 # cycle, no tail
+    ([1, -1, -1], 0),            # two lists
+    ([1, 2, 0, -1], 0),          # cycle plus a tail nobody reaches
+    ([5, -1], 0),                # successor out of range
+    ([2, 2, -1], 0),             # two elements share a successor
+])
+def test_lr_invalid(succ, head):
+    with pytest.raises(oracle.OracleInvalid):
+        oracle.lr_rank(np.array(succ, np.int32), head)
+
+
+def test_lr_pins_reject_mutants():
+    # each plausible oracle mistake must break one of the pins used above
+    succ, head, perm = gen.list_random(1000, 5, with_perm=True)
+    good = oracle.lr_rank(succ, head)
+    mutants = [good + 1, (len(succ) - 1) - good, np.roll(good, 1), good[::-1].copy()]
+    for bad in mutants:
+        with pytest.raises(AssertionError):
+            pins.lr_invariants(succ, head, bad)
+
+
+# ------------------------------------------------------------ components --
+
+def test_cc_golden():
+    g = _read_golden("cc_small.txt")
+    n = int(g["n"][0])
+    for f in (oracle.cc_bfs, oracle.cc_uf):
+        assert np.array_equal(f(g["src"], g["dst"], n), g["label"])
+
+
+def test_cc_brute_force_all_graphs_on_5_vertices():
+    n = 5
+    pairs = list(itertools.combinations(range(n), 2))
+    for mask in range(1 << len(pairs)):
+        edges = [pairs[b] for b in range(len(pairs)) if mask >> b & 1]
+        src = np.array([e[0] for e in edges], np.int32)
+        dst = np.array([e[1] for e in edges], np.int32)
+        # reachability by boolean closure, label = smallest reachable id
+        reach = np.eye(n, dtype=bool)
+        for a, b in edges:
+            reach[a, b] = reach[b, a] = True
+        for k in range(n):
+            reach |= reach[:, [k]] & reach[[k], :]
+        expect = np.array([np.flatnonzero(reach[v])[0] for v in range(n)])
+        assert np.array_equal(oracle.cc_bfs(src, dst, n), expect)
+        assert np.array_equal(oracle.cc_uf(src, dst, n), expect)
+
+
+@pytest.mark.parametrize("k,seg,cycle", [(1, 50, True), (7, 13, False), (40, 25, True), (300, 1, False)])
+def test_cc_k_disjoint_segments(k, seg, cycle):
+    # k disjoint paths (or cycles) over a random relabelling: exactly k labels,
+    # each the smallest id of its segment
+    n = k * seg
+    relabel = gen.permutation(n, 11)
+    src, dst = [], []
+    for s in range(k):
+        ids = relabel[s * seg:(s + 1) * seg]
+        for a, b in zip(ids, ids[1:]):
+            src.append(a); dst.append(b)
+        if cycle and seg > 2:
+            src.append(ids[-1]); dst.append(ids[0])
+    src, dst = np.array(src, np.int32), np.array(dst, np.int32)
+    order = gen.permutation(len(src), 12)
+    src, dst = src[order], dst[order]
+    for f in (oracle.cc_bfs, oracle.cc_uf):
+        label = f(src, dst, n)
+        assert len(np.unique(label)) == k
+        for s in range(k):
+            ids = relabel[s * seg:(s + 1) * seg]
+            assert (label[ids] == ids.min()).all()
+
+
+def test_cc_matches_scipy():
+    sp = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    for seed, (n, m) in enumerate([(1000, 600), (5000, 5000), (1 << 14, 1 << 15)]):
+        src, dst = gen.er(n, m, 100 + seed)
+        a = sp.coo_matrix((np.ones(m), (src, dst)), shape=(n, n))
+        ncomp, comp = csgraph.connected_components(a, directed=False)
+        first = np.full(ncomp, n, np.int64)
+        np.minimum.at(first, comp, np.arange(n))
+        expect = first[comp]
+        assert np.array_equal(oracle.cc_bfs(src, dst, n), expect)
+        assert np.array_equal(oracle.cc_uf(src, dst, n), expect)
+
+
+def test_cc_bfs_equals_uf_er_and_rmat():
+    src, dst = gen.er(1 << 16, 1 << 17, 3)
+    a = oracle.cc_bfs(src, dst, 1 << 16)
+    assert np.array_equal(a, oracle.cc_uf(src, dst, 1 << 16))
+    pins.cc_invariants(src, dst, 1 << 16, a)
+    src, dst, n = workloads.cc_rmat(12, 16)
+    a = oracle.cc_bfs(src, dst, n)
+    assert np.array_equal(a, oracle.cc_uf(src, dst, n))
+    pins.cc_invariants(src, dst, n, a)
+
+
+def test_cc_er_isolated_fraction():
+    # each vertex misses all 2m endpoints with probability (1-1/n)^(2m) ~ e^(-2m/n)
+    n, m = 1 << 16, 1 << 18
+    src, dst = gen.er(n, m, 9)
+    label = oracle.cc_uf(src, dst, n)
+    deg = np.bincount(src, minlength=n) + np.bincount(dst, minlength=n)
+    isolated = (deg == 0).sum()
+    expect = n * np.exp(-2 * m / n)
+    assert abs(isolated - expect) < 6 * np.sqrt(expect) + 3
+    singletons = np.bincount(label, minlength=n)[label] == 1
+    assert singletons.sum() >= isolated
+
+
+def test_cc_edge_cases():
+    e = np.empty(0, np.int32)
+    assert np.array_equal(oracle.cc_uf(e, e, 5), np.arange(5))
+    assert np.array_equal(oracle.cc_bfs(e, e, 5), np.arange(5))
+    assert oracle.cc_uf(e, e, 0).shape == (0,)
+    s = np.array([3, 3, 1], np.int32)
+    d = np.array([3, 1, 3], np.int32)   # self-loop and duplicate edge
+    assert np.array_equal(oracle.cc_uf(s, d, 4), [0, 1, 2, 1])
+    with pytest.raises(oracle.OracleInvalid):
+        oracle.cc_uf(np.array([0], np.int32), np.array([4], np.int32), 4)
+
+
+def test_cc_pins_reject_mutants():
+    src, dst = gen.er(2000, 1500, 4)
+    good = oracle.cc_uf(src, dst, 2000)
+    v = np.arange(2000)
+    big = np.bincount(good).argmax()
+    members = np.flatnonzero(good == big)
+    split = good.copy()
+    split[members[1:][::2]] = members[1]          # a component broken in two
+    mutants = [np.maximum(good, v), v.copy(), split]
+    for bad in mutants:
+        with pytest.raises(AssertionError):
+            pins.cc_invariants(src, dst, 2000, bad)
+
+
+# ------------------------------------------------------------- batches --
+
+def test_batched_oracles_match_single():
+    sizes = gen.loguniform_sizes(20, 2, 10, 3)
+    succ, off, heads = gen.list_batch(sizes, 4)
+    rank = oracle.lr_rank_batched(succ, off, heads)
+    for k in range(len(sizes)):
+        b, e = off[k], off[k + 1]
+        assert np.array_equal(rank[b:e], oracle.lr_rank(succ[b:e], heads[k]))
+    src, dst, eoff, voff = gen.er_batch(sizes, 2, 1, 5)
+    lab = oracle.cc_batched(src, dst, eoff, voff)
+    assert np.array_equal(lab, oracle.cc_batched(src, dst, eoff, voff, use_uf=False))
+    for k in range(len(sizes)):
+        vb, ve, eb, ee = voff[k], voff[k + 1], eoff[k], eoff[k + 1]
+        assert np.array_equal(lab[vb:ve], oracle.cc_bfs(src[eb:ee], dst[eb:ee], ve - vb))

@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of list ranking + connected components on GB300.
+
+One step = lr_rank on a random-layout list of 2^28 elements followed by
+cc_label on an R-MAT graph with 2^24 vertices and 2^28 edges (the large
+plain-instance workload); ``--workload small`` uses a 2^20-element list and a
+uniform random graph with 2^20 vertices and 2^22 edges instead. The value is
+(list elements + graph edges) per second over the timed steps, with the
+inputs resident in HBM; ``e2e`` repeats the measurement with the inputs copied
+from pinned host memory and the results copied back inside every step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+Under torchrun every rank runs its own replica (the single instances do not
+shard) and rank 0 prints one JSON line with the max step time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LR Mnodes/s and CC Medges/s at 1 GB300, % of HBM roofline; batched vs per-launch"
+UNIT = "M(list nodes + graph edges)/s"
+
+# ncu DRAM bytes of one rs_walk (level 0) launch at n = 2^28, random layout:
+# dram__bytes_read.sum + dram__bytes_write.sum, and the hash of lr.cu they were
+# taken from. The figure is reported only while lr.cu is unchanged.
+NCU_WALK0 = {"lr_cu_sha1": None, "bytes_per_launch": None}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--workload", choices=["large", "small"], default="large")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from gen import workloads
+    if name == "large":
+        t = time.time()
+        succ, head = workloads.lr_random(28)
+        src, dst, n_cc = workloads.cc_rmat(24, 16)
+        log(f"inputs generated in {time.time() - t:.1f} s")
+        cfg = {"workload": "lr_random_2p28+cc_rmat_s24_ef16",
+               "lr": {"n": len(succ), "layout": "uniform random permutation", "seed": 3},
+               "cc": {"n": n_cc, "m": len(src), "generator": "R-MAT (0.57, 0.19, 0.19, 0.05), ids permuted",
+                      "seed": 4}}
+    else:
+        succ, head = workloads.lr_random(20)
+        src, dst, n_cc = workloads.cc_er(20, 22)
+        cfg = {"workload": "lr_random_2p20+cc_er_2p20_2p22",
+               "lr": {"n": len(succ), "layout": "uniform random permutation", "seed": 1},
+               "cc": {"n": n_cc, "m": len(src), "generator": "uniform endpoints", "seed": 2}}
+    return succ, head, src, dst, n_cc, cfg
+
+
+def cpu_sample(name):
+    """Bounded sample of the workload for the oracle (about 10 s of CPU work)."""
+    from gen import workloads
+    import gen
+    if name == "large":
+        succ, head = gen.list_random(1 << 25, 3)
+        src, dst, n_cc = workloads.cc_rmat(24, 16)
+        src, dst = src[: 1 << 24].copy(), dst[: 1 << 24].copy()
+        desc = ("oracle walk of a 2^25-element random-layout list + union-find over the first 2^24 edges "
+                "of the R-MAT scale-24 edge list (2^24 vertices)")
+    else:
+        succ, head = workloads.lr_random(20)
+        src, dst, n_cc = workloads.cc_er(20, 22)
+        desc = "oracle on the full small workload (2^20 list, 2^20/2^22 graph)"
+    return succ, head, src, dst, n_cc, desc
+
+
+def time_oracle(sample):
+    import oracle
+    succ, head, src, dst, n_cc, _ = sample
+    t0 = time.perf_counter()
+    oracle.lr_rank(succ, head)
+    t1 = time.perf_counter()
+    oracle.cc_uf(src, dst, n_cc)
+    t2 = time.perf_counter()
+    return t2 - t0, t1 - t0, t2 - t1
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def file_sha1(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = cpu_sample(args.workload)
+    units = len(sample[0]) + len(sample[2])
+    for _ in range(args.warmup):
+        time_oracle(sample)
+    t = [time_oracle(sample)[0] for _ in range(args.steps)]
+    total = sum(t)
+    value = units * args.steps / total / 1e6
+    cfg = workload_config_only(args.workload)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample[5]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config_only(name):
+    if name == "large":
+        return {"workload": "lr_random_2p28+cc_rmat_s24_ef16", "lr": {"n": 1 << 28}, "cc": {"n": 1 << 24, "m": 1 << 28}}
+    return {"workload": "lr_random_2p20+cc_er_2p20_2p22", "lr": {"n": 1 << 20}, "cc": {"n": 1 << 20, "m": 1 << 22}}
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        log("warmup raised to 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1002_4482_gb300 as lrcc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    succ_h, head, src_h, dst_h, n_cc, cfg = workload(args.workload)
+    n_lr, m_cc = len(succ_h), len(src_h)
+    units = n_lr + m_cc
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        succ = torch.from_numpy(succ_h).to(dev)
+        src = torch.from_numpy(src_h).to(dev)
+        dst = torch.from_numpy(dst_h).to(dev)
+        rank_out = torch.empty(n_lr, dtype=torch.int32, device=dev)
+        label = torch.empty(n_cc, dtype=torch.int32, device=dev)
+    stream.synchronize()
+
+    def step():
+        lrcc.lr_rank(succ, head, out=rank_out, stream=stream)
+        lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
+
+    # warm-up (also builds the graphs and the workspace)
+    lrcc.set_timing(True)
+    for _ in range(args.warmup):
+        step()
+    lrcc.check(stream)
+    lrcc.phase_times(stream)
+    lr_stats = None
+
+    # timed region: K steps, events on the launching stream, clocks sampled
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.summary()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    phases = lrcc.phase_times(stream)
+    lrcc.set_timing(False)
+    lrcc.check(stream)
+    ms_step = max_over_ranks(ms_step)
+    value = units * world / (ms_step / 1e3) / 1e6
+
+    # per-part facts
+    lrcc.lr_rank(succ, head, out=rank_out, stream=stream)
+    lr_stats = lrcc.last_stats(stream)
+    lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
+    cc_stats = lrcc.last_stats(stream)
+    lrcc.check(stream)
+
+    lr_ms = sum(v[0] for k, v in phases.items() if k.startswith(("rs_", "lr_small"))) / args.steps
+    cc_ms = sum(v[0] for k, v in phases.items() if k.startswith("cc_")) / args.steps
+    launches_lr = sum(v[1] for k, v in phases.items() if k.startswith(("rs_", "lr_small")))
+    launches_cc = args.steps * (1 + 3 * cc_stats["rounds"])
+
+    hbm, peak_kind = peaks()
+    roofline = None
+    if "rs_walk0" in phases:
+        wt, wl = phases["rs_walk0"]
+        per_launch_ms = wt / wl
+        r1 = lr_stats["splitters"][0] if lr_stats["splitters"] else 0
+        alg_bytes = 16 * n_lr + 16 * r1
+        achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+        traffic = None
+        if NCU_WALK0["lr_cu_sha1"] == file_sha1(os.path.join(ROOT, "paper_1002_4482_gb300", "csrc", "lr.cu")) \
+                and args.workload == "large":
+            traffic = NCU_WALK0["bytes_per_launch"]
+        roofline = {"kernel": "rs_walk (level 0)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                    "ms_per_launch": per_launch_ms,
+                    "algorithmic_bytes": "16 B per list element (read + write back its 8-byte walk word) "
+                                         "+ 16 B per splitter"}
+
+    # ordered control and Wyllie baseline on the same list size (not part of the step)
+    extra = {}
+    if rank == 0:
+        def timed(fn, reps=3):
+            fn()
+            stream.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            stream.synchronize()
+            return a.elapsed_time(b) / reps
+        ms_wy = timed(lambda: lrcc.lr_rank_wyllie(succ, head, out=rank_out, stream=stream), reps=2)
+        lrcc.check(stream)
+        from gen import workloads
+        osucc, ohead = workloads.lr_ordered(28 if args.workload == "large" else 20)
+        del succ
+        torch.cuda.empty_cache()
+        osucc_d = torch.from_numpy(osucc).to(dev)
+        ms_ord = timed(lambda: lrcc.lr_rank(osucc_d, ohead, out=rank_out, stream=stream))
+        lrcc.check(stream)
+        extra = {"lr_wyllie_ms": ms_wy, "lr_wyllie_mnodes_per_s": n_lr / ms_wy / 1e3,
+                 "lr_ordered_ms": ms_ord, "lr_ordered_mnodes_per_s": n_lr / ms_ord / 1e3}
+        del osucc_d
+        succ = torch.from_numpy(succ_h).to(dev)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        succ_p = torch.from_numpy(succ_h).pin_memory()
+        src_p = torch.from_numpy(src_h).pin_memory()
+        dst_p = torch.from_numpy(dst_h).pin_memory()
+        rank_p = torch.empty(n_lr, dtype=torch.int32).pin_memory()
+        label_p = torch.empty(n_cc, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                succ.copy_(succ_p, non_blocking=True)
+                src.copy_(src_p, non_blocking=True)
+                dst.copy_(dst_p, non_blocking=True)
+                lrcc.lr_rank(succ, head, out=rank_out, stream=stream)
+                lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
+                rank_p.copy_(rank_out, non_blocking=True)
+                label_p.copy_(label, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        stream.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        stream.synchronize()
+        barrier()
+        lrcc.check(stream)
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps)
+        if rank == 0:
+            assert rank_p[head].item() == n_lr - 1
+        e2e = {"value": units * world / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": 4 * n_lr + 8 * m_cc, "d2h_bytes_per_step": 4 * n_lr + 4 * n_cc}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = cpu_sample(args.workload)
+        t, tl, tc = time_oracle(sample)
+        cpu = {"value": (len(sample[0]) + len(sample[2])) / t / 1e6, "unit": UNIT, "cores": 1,
+               "kind": "oracle", "sample": sample[5], "seconds": t, "lr_seconds": tl, "cc_seconds": tc,
+               "host_cores": os.cpu_count()}
+
+    if rank == 0:
+        cfg.update({"l2": "inputs larger than L2 (4n B list, 8m B edges); no flush between steps",
+                    "parallelism": f"replicas x{world}", "stream": "one non-default stream",
+                    "timing": "CUDA events on the launching stream; phase events inside the library"})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generators in gen/)",
+                "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_lr + launches_cc,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "lr": {"ms": lr_ms, "mnodes_per_s": n_lr / lr_ms / 1e3 if lr_ms else None,
+                       "problem_bytes_frac": 8 * n_lr / (lr_ms / 1e3) / 1e9 / hbm if lr_ms else None,
+                       "levels": lr_stats["levels"], "splitters": lr_stats["splitters"]},
+                "cc": {"ms": cc_ms, "medges_per_s": m_cc / cc_ms / 1e3 if cc_ms else None,
+                       "problem_bytes_frac": (8 * m_cc + 4 * n_cc) / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
+                       "rounds": cc_stats["rounds"]},
+                "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+                **extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

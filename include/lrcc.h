@@ -1,0 +1,184 @@
+/*
+ * lrcc — list ranking and connected components on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of liblrcc.so. Every array argument is a DEVICE pointer owned by the
+ * caller; inputs are read only and never modified; outputs are written in
+ * full. Calls are asynchronous on `stream` (a cudaStream_t passed as void*,
+ * NULL = the legacy default stream): a call returns once its work is
+ * enqueued. Node and vertex ids are int32 (at most 2^31 - 2 of them); counts
+ * are int64 so that batched totals may exceed 2^31.
+ *
+ * Errors. Argument errors that the host can see (a NULL pointer with a
+ * non-zero size, a negative size, a head outside [0, n), a size above the
+ * id range) return at once and enqueue nothing. Errors that only the device
+ * can see (the input is not a single list, an id is out of range, the
+ * component loop hit its round cap) are recorded in a status word that
+ * belongs to the stream; lrcc_last_status() waits for the stream and returns
+ * and clears it. After any error the outputs are undefined.
+ *
+ * Workspace. The library keeps one workspace per (device, stream): it is
+ * allocated with cudaMalloc on the first call that needs it, grown when a
+ * later call needs more, and freed by lrcc_release(stream). Calls on the same
+ * stream share it safely because they are ordered; calls on different streams
+ * use different workspaces. The first call on a stream therefore allocates
+ * and must not be made during stream capture.
+ */
+#ifndef LRCC_H
+#define LRCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lrcc_status {
+    LRCC_OK = 0,
+    LRCC_ERR_ARG = 1,            /* bad argument, detected on the host */
+    LRCC_ERR_NOMEM = 2,          /* workspace allocation failed */
+    LRCC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    LRCC_ERR_INVALID_INPUT = 4,  /* not a list / id out of range, detected on the device */
+    LRCC_ERR_NOT_CONVERGED = 5,  /* the component loop reached its round cap */
+    LRCC_ERR_TIMEOUT = 6         /* a bounded device-side wait gave up */
+} lrcc_status;
+
+/* Human-readable name of a status code. Never NULL. */
+const char* lrcc_status_str(int status);
+
+/* ABI version of this header (major * 100 + minor). */
+int lrcc_version(void);
+
+/*
+ * List ranking (Sec. 3 of Dehne & Yogaratnam, "Exploring the Limits of GPUs
+ * With Parallel Graph Algorithms"): the list is stored as a successor array;
+ * the rank of an element is its distance to the last element of the list.
+ *
+ *   succ  int32[n]  successor of each element; the tail has succ = -1 (the
+ *                   paper's convention succ[j] = j is accepted as a tail too)
+ *   n              number of elements; the input must be ONE list holding
+ *                   all n elements, otherwise LRCC_ERR_INVALID_INPUT is
+ *                   recorded on the stream
+ *   head            index of the first element, in [0, n)
+ *   rank  int32[n]  output: rank[i] = number of links from i to the tail
+ *                   (head: n - 1, tail: 0)
+ *
+ * lr_rank uses the sparse ruling set / random splitter method (Sec. 3.2,
+ * Algorithm 2 and Algorithm 3): random splitters cut the list into sublists,
+ * each sublist is walked once, the list of splitters is ranked recursively
+ * and the ranks are expanded back. Expected work O(n).
+ */
+lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
+
+/*
+ * Same contract, computed by Wyllie's pointer jumping (Sec. 3.1,
+ * Algorithm 1): ceil(log2 n) rounds of rank[i] += rank[succ[i]],
+ * succ[i] = succ[succ[i]] over packed 64-bit (rank, successor) words.
+ * O(n log n) work; kept as the baseline the paper compares against.
+ */
+lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
+
+/*
+ * Connected components (Sec. 4, Algorithm 4, after Shiloach and Vishkin) of
+ * an undirected graph given as an edge list.
+ *
+ *   src, dst  int32[m]  edge e joins src[e] and dst[e]; ids in [0, n);
+ *                       self-loops and repeated edges are allowed
+ *   m, n                edge and vertex counts
+ *   label     int32[n]  output: the smallest vertex id of the component of
+ *                       each vertex. It is also the working parent array.
+ *
+ * Method: parent[v] = v; then rounds of hooking (for every edge whose
+ * endpoints have different roots, atomicMin links the larger root below the
+ * smaller) and shortcutting (pointer jumping until every tree is a star),
+ * until a hook pass finds no edge joining two roots. The round count is
+ * capped; reaching the cap records LRCC_ERR_NOT_CONVERGED.
+ */
+lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
+                     int32_t* label, void* stream);
+
+/*
+ * Batched list ranking: num_lists independent lists in one launch.
+ * List k owns elements [node_off[k], node_off[k+1]) of succ and rank;
+ * succ values and heads[k] are LOCAL ids (0-based within list k), and the
+ * ranks are local too. node_off is int64[num_lists + 1] on the device,
+ * non-decreasing, node_off[0] = 0. Every list must be valid.
+ */
+lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
+                            int64_t num_lists, int32_t* rank, void* stream);
+
+/*
+ * Batched connected components: num_graphs independent graphs in one launch.
+ * Graph k owns edges [edge_off[k], edge_off[k+1]) of src/dst and vertices
+ * [vert_off[k], vert_off[k+1]) of label; edge endpoints and labels are LOCAL
+ * ids. Offsets are int64[num_graphs + 1] on the device, non-decreasing, 0 first.
+ */
+lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
+                             const int64_t* vert_off, int64_t num_graphs, int32_t* label,
+                             void* stream);
+
+/*
+ * Waits for `stream`, then returns and clears the device status word of its
+ * workspace (LRCC_OK if nothing was recorded since the last call).
+ */
+lrcc_status lrcc_last_status(void* stream);
+
+/* Statistics of the most recent call on `stream` (waits for the stream). */
+typedef struct lrcc_stats {
+    int32_t kind;            /* 1 = lr_rank, 2 = lr_rank_wyllie, 3 = cc_label, 4/5 = batched */
+    int32_t levels;          /* lr_rank: ruling-set levels before the one-block rank */
+    int64_t splitters[8];    /* lr_rank: splitters chosen at each level */
+    int32_t rounds;          /* cc_label: hook passes (including the final, quiet one) */
+    int32_t jump_rounds;     /* lr_rank_wyllie: pointer-jumping rounds */
+} lrcc_stats;
+lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out);
+
+/*
+ * Tuning knobs (a process-wide table indexed by ceil(log2 n)). Any field set
+ * to 0 keeps the library's default for that field.
+ */
+typedef struct lrcc_plan {
+    int32_t rs_spacing0;     /* mean sublist length at the first ruling-set level */
+    int32_t rs_spacing;      /* mean sublist length at deeper levels */
+    int32_t rs_small;        /* lists of at most this many elements are ranked by one block */
+    int32_t rs_chains;       /* sublist walks interleaved per thread: 1, 2 or 4 */
+    int32_t cc_hook;         /* 1 = one atomicMin per edge and pass, 2 = re-link until joined */
+    int32_t cc_max_rounds;   /* cap on hook passes (-1 = back to the automatic cap) */
+    int32_t use_graphs;      /* 1 = replay captured CUDA graphs, 2 = plain launches */
+    int32_t reserved;
+    uint64_t seed;           /* splitter seed (results do not depend on it) */
+} lrcc_plan;
+
+/* kind: 1 = list ranking, 3 = connected components; sizes with ceil(log2 n)
+ * in [log2_lo, log2_hi] get `plan`. */
+lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* plan);
+lrcc_status lrcc_get_plan(int kind, int64_t n, lrcc_plan* out);
+
+/*
+ * Phase timing. While enabled (process-wide), list-ranking calls launch their
+ * kernels directly (no graph replay) and record a pair of CUDA events around
+ * every kernel on the caller's stream; component calls record events around
+ * the initialisation and around the whole device-side hook/shortcut loop.
+ * lrcc_phase_times() waits for `stream`, adds the elapsed time and launch
+ * count of every phase recorded since the previous query into ms_total[p]
+ * and launches[p] (arrays of at least lrcc_phase_count() entries) and
+ * forgets the recorded events.
+ */
+lrcc_status lrcc_set_timing(int enable);
+int lrcc_phase_count(void);
+const char* lrcc_phase_name(int phase);
+lrcc_status lrcc_phase_times(void* stream, double* ms_total, int64_t* launches);
+
+/* Frees the workspace and cached graphs of `stream` (waits for it first). */
+lrcc_status lrcc_release(void* stream);
+
+/* Bytes of device workspace currently held by the library (all streams). */
+int64_t lrcc_workspace_bytes(void);
+
+/* Device workspace a call of the given kind and size would need. */
+int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRCC_H */

@@ -1,0 +1,257 @@
+"""GB300-native list ranking and connected components.
+
+Thin Python binding over the C ABI of ``liblrcc.so`` (declared in
+``include/lrcc.h``). Every function here only marshals arguments: tensors are
+checked for dtype, device and layout, their device pointers and the current
+CUDA stream are passed to the C entry point of the same name, and a non-OK
+status raises :class:`LrccError`. All computation happens in the CUDA kernels
+of ``csrc/``; there is no CPU fallback, and importing the binding on a
+machine without the built library raises at first use.
+
+Calls are asynchronous on the current stream. Errors that only the device can
+detect (an input that is not a single list, an out-of-range id, a loop that
+hit its round cap) are reported by :func:`check` / :func:`last_status`, which
+wait for the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "liblrcc.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(7)
+KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
+
+SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "cc_label",
+           "lr_rank_batched", "cc_label_batched", "lrcc_last_status", "lrcc_last_stats",
+           "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
+           "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
+           "lrcc_phase_times")
+
+
+class LrccError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} (status {status})")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("splitters", ctypes.c_int64 * 8), ("rounds", ctypes.c_int32),
+                ("jump_rounds", ctypes.c_int32)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("rs_spacing0", ctypes.c_int32), ("rs_spacing", ctypes.c_int32),
+                ("rs_small", ctypes.c_int32), ("rs_chains", ctypes.c_int32),
+                ("cc_hook", ctypes.c_int32), ("cc_max_rounds", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load liblrcc.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        p, i64, i32, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        lib.lrcc_status_str.argtypes = [i]
+        lib.lrcc_status_str.restype = ctypes.c_char_p
+        lib.lrcc_version.restype = i
+        lib.lr_rank.argtypes = [p, i64, i32, p, p]
+        lib.lr_rank_wyllie.argtypes = [p, i64, i32, p, p]
+        lib.cc_label.argtypes = [p, p, i64, i64, p, p]
+        lib.lr_rank_batched.argtypes = [p, p, p, i64, p, p]
+        lib.cc_label_batched.argtypes = [p, p, p, p, i64, p, p]
+        lib.lrcc_last_status.argtypes = [p]
+        lib.lrcc_last_stats.argtypes = [p, ctypes.POINTER(Stats)]
+        lib.lrcc_set_plan.argtypes = [i, i, i, ctypes.POINTER(Plan)]
+        lib.lrcc_get_plan.argtypes = [i, i64, ctypes.POINTER(Plan)]
+        lib.lrcc_release.argtypes = [p]
+        lib.lrcc_workspace_bytes.restype = i64
+        lib.lrcc_workspace_query.argtypes = [i, i64, i64]
+        lib.lrcc_workspace_query.restype = i64
+        lib.lrcc_set_timing.argtypes = [i]
+        lib.lrcc_phase_count.restype = i
+        lib.lrcc_phase_name.argtypes = [i]
+        lib.lrcc_phase_name.restype = ctypes.c_char_p
+        lib.lrcc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        for f in ("lr_rank", "lr_rank_wyllie", "cc_label", "lr_rank_batched", "cc_label_batched",
+                  "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
+                  "lrcc_release", "lrcc_set_timing", "lrcc_phase_times"):
+            getattr(lib, f).restype = i
+        _lib = lib
+        return lib
+
+
+def status_str(status: int) -> str:
+    return load().lrcc_status_str(int(status)).decode()
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_i32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA int32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _dev_i64(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA int64 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _out(out, n, like, name):
+    if out is None:
+        return torch.empty(n, dtype=torch.int32, device=like.device)
+    _dev_i32(out, name)
+    if out.numel() != n:
+        raise ValueError(f"{name} must hold {n} elements")
+    return out
+
+
+def _call(status: int, what: str):
+    if status != OK:
+        raise LrccError(status, what)
+
+
+def lr_rank(succ: torch.Tensor, head: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Ranks (distance to the tail) of the list stored in ``succ`` (sparse ruling set)."""
+    _dev_i32(succ, "succ")
+    rank = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_rank(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), _stream(stream)), "lr_rank")
+    return rank
+
+
+def lr_rank_wyllie(succ: torch.Tensor, head: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Same result as :func:`lr_rank`, by Wyllie pointer jumping."""
+    _dev_i32(succ, "succ")
+    rank = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_rank_wyllie(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), _stream(stream)),
+          "lr_rank_wyllie")
+    return rank
+
+
+def cc_label(src: torch.Tensor, dst: torch.Tensor, n: int, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """Smallest vertex id of each vertex's connected component."""
+    _dev_i32(src, "src")
+    _dev_i32(dst, "dst")
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst must have the same length")
+    label = _out(out, n, src, "out")
+    _call(load().cc_label(src.data_ptr(), dst.data_ptr(), src.numel(), int(n), label.data_ptr(), _stream(stream)),
+          "cc_label")
+    return label
+
+
+def lr_rank_batched(succ: torch.Tensor, node_off: torch.Tensor, heads: torch.Tensor,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Ranks of independent lists concatenated in ``succ`` (local ids, int64 offsets)."""
+    _dev_i32(succ, "succ")
+    _dev_i64(node_off, "node_off")
+    _dev_i32(heads, "heads")
+    if node_off.numel() != heads.numel() + 1:
+        raise ValueError("node_off must have len(heads) + 1 entries")
+    rank = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_rank_batched(succ.data_ptr(), node_off.data_ptr(), heads.data_ptr(), heads.numel(),
+                                 rank.data_ptr(), _stream(stream)), "lr_rank_batched")
+    return rank
+
+
+def cc_label_batched(src: torch.Tensor, dst: torch.Tensor, edge_off: torch.Tensor, vert_off: torch.Tensor,
+                     n_total: int | None = None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Min-id component labels of independent graphs (local ids, int64 offsets)."""
+    _dev_i32(src, "src")
+    _dev_i32(dst, "dst")
+    _dev_i64(edge_off, "edge_off")
+    _dev_i64(vert_off, "vert_off")
+    if edge_off.numel() != vert_off.numel():
+        raise ValueError("edge_off and vert_off must have the same length")
+    if n_total is None:
+        n_total = int(vert_off[-1].item())
+    label = _out(out, n_total, src, "out")
+    _call(load().cc_label_batched(src.data_ptr(), dst.data_ptr(), edge_off.data_ptr(), vert_off.data_ptr(),
+                                  vert_off.numel() - 1, label.data_ptr(), _stream(stream)), "cc_label_batched")
+    return label
+
+
+def last_status(stream=None) -> int:
+    """Waits for the stream; returns and clears its device status word."""
+    return int(load().lrcc_last_status(_stream(stream)))
+
+
+def check(stream=None) -> None:
+    """Raises LrccError if the device recorded an error on this stream."""
+    st = last_status(stream)
+    if st != OK:
+        raise LrccError(st, "device")
+
+
+def last_stats(stream=None) -> dict:
+    s = Stats()
+    _call(load().lrcc_last_stats(_stream(stream), ctypes.byref(s)), "lrcc_last_stats")
+    return {"kind": s.kind, "levels": s.levels, "splitters": list(s.splitters)[: s.levels],
+            "rounds": s.rounds, "jump_rounds": s.jump_rounds}
+
+
+def set_plan(kind: int, log2_lo: int = 0, log2_hi: int = 32, **fields) -> None:
+    p = Plan(**fields)
+    _call(load().lrcc_set_plan(kind, log2_lo, log2_hi, ctypes.byref(p)), "lrcc_set_plan")
+
+
+def get_plan(kind: int, n: int) -> dict:
+    p = Plan()
+    _call(load().lrcc_get_plan(kind, n, ctypes.byref(p)), "lrcc_get_plan")
+    return {f: getattr(p, f) for f, _ in Plan._fields_ if f != "reserved"}
+
+
+def release(stream=None) -> None:
+    _call(load().lrcc_release(_stream(stream)), "lrcc_release")
+
+
+def workspace_bytes() -> int:
+    return int(load().lrcc_workspace_bytes())
+
+
+def workspace_query(kind: int, n: int, m: int = 0) -> int:
+    return int(load().lrcc_workspace_query(kind, n, m))
+
+
+def set_timing(enable: bool) -> None:
+    """Phase timing: CUDA events around every kernel (list ranking) or loop (components)."""
+    _call(load().lrcc_set_timing(1 if enable else 0), "lrcc_set_timing")
+
+
+def phase_times(stream=None) -> dict:
+    """Waits for the stream; {phase: (total_ms, launches)} recorded since the last query."""
+    lib = load()
+    k = lib.lrcc_phase_count()
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_int64 * k)()
+    _call(lib.lrcc_phase_times(_stream(stream), ms, cnt), "lrcc_phase_times")
+    return {lib.lrcc_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(k) if cnt[i]}

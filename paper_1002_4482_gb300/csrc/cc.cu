@@ -1,0 +1,330 @@
+// Connected components (Sec. 4, Algorithm 4), restated for sm_103a.
+//
+// The parent array is the caller's label array. Each round is
+//   hook      stream the edge list in 16-byte vectors (evict-first in L2 so
+//             the parent array stays resident); for an edge whose endpoints
+//             have different parents, atomicMin links the larger root below
+//             the smaller one (priority write in place of the paper's
+//             "arbitrary" concurrent write);
+//   shortcut  pointer jumping until every tree is a star (SV steps 1a / 4);
+//   control   a one-thread kernel reads the change flag (SV step 5, raised by
+//             one warp-ballot store per warp) and sets the condition of a
+//             CUDA-graph while-node, so the loop runs without the host.
+// Links always point from a larger id to a smaller one, so no cycle can form
+// and every root is the smallest id of its tree; when a pass finds no edge
+// between two trees the trees are the components and the roots their
+// minimum-id labels.
+//
+// Hook rules (plan.cc_hook): 1 = one atomicMin per edge and pass, as in the
+// Shiloach-Vishkin round structure; 2 = when the atomicMin finds that the
+// larger root was linked meanwhile, keep joining (old parent, smaller root)
+// until one link lands, so each pass joins every edge and the next pass only
+// confirms. Both give the same labels.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrcc {
+
+namespace {
+
+constexpr int BLOCK = 256;
+
+template <bool VEC>
+__global__ void __launch_bounds__(BLOCK) cc_init(int32_t* __restrict__ parent, int64_t n) {
+    const int64_t ngroups = (n + 3) >> 2;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
+         g += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int64_t i0 = g * 4;
+        if (VEC && i0 + 3 < n) {
+            *reinterpret_cast<int4*>(parent + i0) =
+                make_int4((int)i0, (int)i0 + 1, (int)i0 + 2, (int)i0 + 3);
+        } else {
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) parent[i0 + q] = (int)(i0 + q);
+        }
+    }
+}
+
+// Follow parents to a root. Every link goes to a smaller id, so the walk
+// ends within n steps on any state the kernels can produce.
+__device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t x) {
+    for (;;) {
+        const int32_t p = ld_cg(parent + x);
+        if (p == x) return x;
+        x = p;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b) {
+    if (a == b) return false;
+    if constexpr (MODE == 1) {
+        atomicMin(parent + max(a, b), min(a, b));
+        return true;
+    } else {
+    for (;;) {
+        a = find_root(parent, a);
+        b = find_root(parent, b);
+        if (a == b) return true;
+        const int32_t hi = max(a, b), lo = min(a, b);
+        const int32_t old = atomicMin(parent + hi, lo);
+        if (old == hi) return true;
+        // hi had been linked below `old` by another thread: join old and lo
+        a = old;
+        b = lo;
+    }
+    }
+}
+
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(BLOCK)
+    cc_hook(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+            int32_t* parent, int64_t n, DevCtl* ctl) {
+    const uint64_t pol = policy_evict_first();
+    const int64_t ngroups = (m + 3) >> 2;
+    bool changed = false;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
+         g += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int64_t e0 = g * 4;
+        int u[4], v[4];
+        if (VEC && e0 + 3 < m) {
+            const int4 a = ld_stream_v4(src + e0, pol);
+            const int4 b = ld_stream_v4(dst + e0, pol);
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+            v[0] = b.x; v[1] = b.y; v[2] = b.z; v[3] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                u[q] = e0 + q < m ? ld_stream(src + e0 + q, pol) : 0;
+                v[q] = e0 + q < m ? ld_stream(dst + e0 + q, pol) : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (u[q] < 0 || u[q] >= n || v[q] < 0 || v[q] >= n) {
+                record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)(e0 + q));
+                u[q] = v[q] = 0;
+            }
+        }
+        int32_t a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = parent[u[q]];
+            b[q] = parent[v[q]];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) changed |= hook_pair<MODE>(parent, a[q], b[q]);
+    }
+    if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) ctl->flag = 1;
+}
+
+// Pointer jumping to stars: parent[v] <- root(v). Roots do not move during
+// this pass and every value read is an ancestor, so one pass suffices.
+template <bool VEC>
+__global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n) {
+    const int64_t ngroups = (n + 3) >> 2;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
+         g += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int64_t i0 = g * 4;
+        if (VEC && i0 + 3 < n) {
+            int4 p = *reinterpret_cast<const int4*>(parent + i0);
+            int* pp = reinterpret_cast<int*>(&p);
+            bool ch = false;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (pp[q] != (int)(i0 + q)) {
+                    const int r = find_root(parent, pp[q]);
+                    ch |= r != pp[q];
+                    pp[q] = r;
+                }
+            }
+            if (ch) *reinterpret_cast<int4*>(parent + i0) = p;
+        } else {
+            for (int q = 0; q < 4; ++q) {
+                const int64_t v = i0 + q;
+                if (v < n) {
+                    const int p = parent[v];
+                    if (p != v) {
+                        const int r = find_root(parent, p);
+                        if (r != p) parent[v] = r;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Loop control on the device: continue while the last hook pass joined
+// something, the round cap is not reached and no error was recorded.
+__global__ void cc_control(DevCtl* ctl, cudaGraphConditionalHandle h, int cap) {
+    const int r = ++ctl->rounds;
+    const int f = ctl->flag;
+    ctl->flag = 0;
+    unsigned cont = f != 0;
+    if (cont && r >= cap) {
+        record_error(ctl, LRCC_ERR_NOT_CONVERGED, r);
+        cont = 0;
+    }
+    if (ctl->status) cont = 0;
+    cudaGraphSetConditional(h, cont);
+}
+
+// Same decision for the host-driven loop: the answer is left in ctl->pad[0].
+__global__ void cc_control_host(DevCtl* ctl, int cap) {
+    const int r = ++ctl->rounds;
+    const int f = ctl->flag;
+    ctl->flag = 0;
+    int cont = f != 0;
+    if (cont && r >= cap) {
+        record_error(ctl, LRCC_ERR_NOT_CONVERGED, r);
+        cont = 0;
+    }
+    if (ctl->status) cont = 0;
+    ctl->pad[0] = cont;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+struct CcArgs {
+    const int32_t* src;
+    const int32_t* dst;
+    int64_t m, n;
+    int32_t* label;
+    int mode;
+    int cap;
+};
+
+// Enqueues one round body: hook, shortcut (control is added by the caller).
+lrcc_status enqueue_round(Ctx* c, cudaStream_t s, const CcArgs& a) {
+    const bool ve = aligned16(a.src) && aligned16(a.dst);
+    const bool vn = aligned16(a.label);
+    const void* hk = a.mode == 1 ? (ve ? (const void*)cc_hook<1, true> : (const void*)cc_hook<1, false>)
+                                 : (ve ? (const void*)cc_hook<2, true> : (const void*)cc_hook<2, false>);
+    const int64_t eg = (a.m + 3) / 4;
+    if (eg > 0) {
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((eg + BLOCK - 1) / BLOCK,
+                                                                  persistent_grid(c, hk, BLOCK)));
+        phase_begin(c, s);
+        if (a.mode == 1) {
+            if (ve) cc_hook<1, true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
+            else cc_hook<1, false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
+        } else {
+            if (ve) cc_hook<2, true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
+            else cc_hook<2, false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
+        }
+        phase_end(c, s, PH_CC_HOOK);
+    }
+    const void* sk = vn ? (const void*)cc_shortcut<true> : (const void*)cc_shortcut<false>;
+    const int64_t ng = (a.n + 3) / 4;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((ng + BLOCK - 1) / BLOCK,
+                                                              persistent_grid(c, sk, BLOCK)));
+    phase_begin(c, s);
+    if (vn) cc_shortcut<true><<<g, BLOCK, 0, s>>>(a.label, a.n);
+    else cc_shortcut<false><<<g, BLOCK, 0, s>>>(a.label, a.n);
+    phase_end(c, s, PH_CC_SHORTCUT);
+    return cuda_status(cudaGetLastError());
+}
+
+lrcc_status build_loop_graph(Ctx* c, const CcArgs& a, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LRCC_ERR_CUDA;
+    cudaGraphConditionalHandle h;
+    lrcc_status st = LRCC_OK;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return LRCC_ERR_CUDA;
+    }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return LRCC_ERR_CUDA;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->capture, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return LRCC_ERR_CUDA;
+    }
+    st = enqueue_round(c, c->capture, a);
+    cc_control<<<1, 1, 0, c->capture>>>(c->ctl, h, a.cap);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->capture, &captured);
+    if (st == LRCC_OK && ce != cudaSuccess) st = LRCC_ERR_CUDA;
+    if (st == LRCC_OK && cudaGraphInstantiate(out, g, 0) != cudaSuccess) st = LRCC_ERR_CUDA;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+}
+
+}  // namespace
+
+lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
+                   int32_t* label, const Plan& p) {
+    CcArgs a{src, dst, m, n, label, p.cc_hook == 1 ? 1 : 2, 0};
+    int lg = 0;
+    while ((int64_t(1) << lg) < n) ++lg;
+    a.cap = p.cc_max_rounds > 0 ? p.cc_max_rounds : 64 + 4 * lg;
+    cudaStream_t s = c->stream;
+    const void* ik = aligned16(label) ? (const void*)cc_init<true> : (const void*)cc_init<false>;
+    const int64_t ng = (n + 3) / 4;
+    const int gi = (int)std::max<int64_t>(1, std::min<int64_t>((ng + BLOCK - 1) / BLOCK,
+                                                               persistent_grid(c, ik, BLOCK)));
+    phase_begin(c, s);
+    if (aligned16(label)) cc_init<true><<<gi, BLOCK, 0, s>>>(label, n);
+    else cc_init<false><<<gi, BLOCK, 0, s>>>(label, n);
+    phase_end(c, s, PH_CC_INIT);
+
+    if (p.use_graphs != 2) {
+        const std::vector<uint64_t> key = {(uint64_t)KIND_CC, (uint64_t)src, (uint64_t)dst, (uint64_t)m,
+                                           (uint64_t)n, (uint64_t)label, (uint64_t)a.mode, (uint64_t)a.cap};
+        GraphEntry* e = nullptr;
+        for (auto& ge : c->graphs)
+            if (ge.key == key) e = &ge;
+        if (!e) {
+            cudaGraphExec_t ex = nullptr;
+            const lrcc_status st = build_loop_graph(c, a, &ex);
+            if (st != LRCC_OK) return st;
+            if (c->graphs.size() >= 16) {
+                auto it = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                           [](const GraphEntry& x, const GraphEntry& y) {
+                                               return x.last_use < y.last_use;
+                                           });
+                cudaGraphExecDestroy(it->exec);
+                c->graphs.erase(it);
+            }
+            c->graphs.push_back(GraphEntry{key, ex, 0});
+            e = &c->graphs.back();
+        }
+        e->last_use = ++c->tick;
+        phase_begin(c, s);
+        const lrcc_status st = cuda_status(cudaGraphLaunch(e->exec, s));
+        phase_end(c, s, PH_CC_LOOP);
+        return st;
+    }
+    // host-driven loop: one flag read per round
+    int* host_flag = nullptr;
+    if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) return LRCC_ERR_NOMEM;
+    lrcc_status st = LRCC_OK;
+    for (int r = 0; r < a.cap + 1; ++r) {
+        st = enqueue_round(c, s, a);
+        if (st != LRCC_OK) break;
+        cc_control_host<<<1, 1, 0, s>>>(c->ctl, a.cap);
+        cudaMemcpyAsync(host_flag, &c->ctl->pad[0], sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            st = LRCC_ERR_CUDA;
+            break;
+        }
+        if (!*host_flag) break;
+    }
+    cudaFreeHost(host_flag);
+    return st;
+}
+
+}  // namespace lrcc

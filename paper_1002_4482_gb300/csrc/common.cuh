@@ -1,0 +1,110 @@
+// Device-side helpers shared by the list-ranking and component kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lrcc.h"
+
+namespace lrcc {
+
+// ---------------------------------------------------------------- control --
+
+// Per-workspace control block in device memory. Zeroed before every call
+// except where noted.
+struct DevCtl {
+    int status;          // first device-detected error (lrcc_status), 0 = none
+    int flag;            // component loop: some edge joined two roots this pass
+    int rounds;          // component loop: hook passes so far
+    int jump_rounds;     // pointer-jumping rounds (stats)
+    int spl_count[8];    // ruling set: non-head splitters claimed at each level
+    int work[8];         // ruling set: next splitter to walk at each level
+    int err_where;       // index that raised the error (debugging aid)
+    int batch_next;      // batched kernels: next instance to take
+    int pad[2];
+};
+
+__device__ __forceinline__ void record_error(DevCtl* c, int code, int where = -1) {
+    if (atomicCAS(&c->status, 0, code) == 0) c->err_where = where;
+}
+
+// ------------------------------------------------------------ packed words --
+
+// List ranking moves (value, pointer) pairs as one 8-byte word so that a jump
+// or a sublist step is a single gather (Sec. 3.1: the 64-bit "union").
+constexpr uint32_t NIL = 0x7FFFFFFFu;   // no successor
+constexpr uint32_t SPL = 0x80000000u;   // low word: this element is a splitter
+constexpr uint32_t VIS = 0x80000000u;   // high word: visited by a sublist walk
+
+__device__ __forceinline__ uint64_t pack(uint32_t lo, uint32_t hi) {
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+__device__ __forceinline__ uint32_t lo32(uint64_t w) { return static_cast<uint32_t>(w); }
+__device__ __forceinline__ uint32_t hi32(uint64_t w) { return static_cast<uint32_t>(w >> 32); }
+
+// ------------------------------------------------------------ cache hints --
+
+// L2 policy for data touched once per pass (edge streams, the input list):
+// evict it first so that the parent / word arrays stay resident.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 16-byte streaming load, read-only path, no L1 allocation, L2 hint.
+__device__ __forceinline__ int4 ld_stream_v4(const int32_t* p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+                 : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Load that bypasses L1 (sees other SMs' atomics sooner than an L1 hit would).
+__device__ __forceinline__ int32_t ld_cg(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_cg_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+// ------------------------------------------------------------------ hash --
+
+// Splitter choice: element i is a splitter when a 32-bit mix of (i, seed)
+// falls below thr = 2^32 / spacing. The mixer is the finaliser of
+// MurmurHash3 (Appleby, public domain). Results never depend on the choice.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ bool pick(uint32_t i, uint32_t seed, uint32_t thr) {
+    return mix32(i * 0x9E3779B1u + seed) < thr;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace lrcc

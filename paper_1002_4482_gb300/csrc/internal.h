@@ -1,0 +1,121 @@
+// Host-side internals shared by the translation units of liblrcc.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lrcc.h"
+
+namespace lrcc {
+
+struct DevCtl;
+
+constexpr int KIND_LR = 1;
+constexpr int KIND_LR_WYLLIE = 2;
+constexpr int KIND_CC = 3;
+constexpr int KIND_LR_BATCH = 4;
+constexpr int KIND_CC_BATCH = 5;
+
+// Resolved tuning knobs (every field set).
+struct Plan {
+    int rs_spacing0 = 32;
+    int rs_spacing = 16;
+    int rs_small = 8192;
+    int rs_chains = 2;
+    int cc_hook = 2;
+    int cc_max_rounds = 0;
+    int use_graphs = 1;
+    uint64_t seed = 0x5eedULL;
+};
+Plan plan_for(int kind, int64_t n);
+
+// Ruling-set level layout for a list of n elements (host-side plan).
+constexpr int MAX_LEVELS = 8;
+struct RsLayout {
+    int levels = 0;                 // L: levels with a walk; level L is ranked by one block
+    int64_t size[MAX_LEVELS + 1];   // element bound of each level (size[0] = n)
+    uint32_t thr[MAX_LEVELS];       // splitter threshold of each walked level
+    size_t off_R[MAX_LEVELS + 1], off_snext[MAX_LEVELS + 1], off_sw[MAX_LEVELS + 1],
+        off_S[MAX_LEVELS + 1];
+    size_t off_W0 = 0;
+    size_t bytes = 0;
+};
+RsLayout rs_layout(int64_t n, const Plan& p);
+
+// Phase ids for timing mode (names in runtime.cu).
+enum Phase {
+    PH_SELECT0, PH_WALK0, PH_SELECT, PH_WALK, PH_FINAL, PH_EXPAND, PH_EXPAND0, PH_SMALL,
+    PH_WY_PACK, PH_WY_JUMP, PH_WY_FINAL, PH_CC_INIT, PH_CC_LOOP, PH_CC_HOOK, PH_CC_SHORTCUT,
+    PH_LR_BATCH, PH_CC_BATCH, PH_BATCH_PREP, PH_COUNT
+};
+
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
+// One workspace per (device, stream).
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;    // the caller's stream this workspace serves
+    cudaStream_t capture = nullptr;   // private stream used to capture graphs
+    DevCtl* ctl = nullptr;            // device control block
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int sms = 0;
+    std::vector<GraphEntry> graphs;
+    uint64_t tick = 0;
+    // host-side facts about the most recent call
+    int last_kind = 0;
+    int last_levels = 0;
+    int64_t last_splitter_cap[MAX_LEVELS] = {};
+    std::mutex mu;                    // serialises host calls that use this workspace
+    // timing mode: events recorded around phases, read by lrcc_phase_times
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    size_t cur_begin = 0;
+    struct Rec { int phase; size_t a, b; };
+    std::vector<Rec> recs;
+};
+
+// Timing mode. phase_begin/phase_end bracket one kernel (or loop) on stream s
+// when timing is on and s is not capturing; they do nothing otherwise.
+bool timing_enabled();
+void phase_begin(Ctx* c, cudaStream_t s);
+void phase_end(Ctx* c, cudaStream_t s, int phase);
+
+// Returns the workspace of `stream` on the current device, creating it.
+lrcc_status ctx_for(void* stream, Ctx** out);
+lrcc_status ensure_ws(Ctx* c, size_t bytes);
+lrcc_status cuda_status(cudaError_t e);
+
+// Persistent grid size for a kernel: SMs x resident blocks per SM.
+int persistent_grid(Ctx* c, const void* kernel, int block, size_t smem = 0);
+
+// --- list ranking (lr.cu)
+lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
+                          int32_t* rank, const Plan& p, const RsLayout& L);
+lrcc_status lr_enqueue_wyllie(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
+                              int32_t* rank, const Plan& p);
+size_t lr_wyllie_ws(int64_t n, const Plan& p);
+
+// --- connected components (cc.cu)
+lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
+                   int32_t* label, const Plan& p);
+
+// --- batched (batch.cu)
+lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, const int32_t* heads,
+                           int64_t count, int32_t* rank, const Plan& p);
+lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const int64_t* eoff,
+                           const int64_t* voff, int64_t count, int32_t* label, const Plan& p);
+size_t lr_batched_ws(int64_t total_nodes);
+size_t cc_batched_ws(int64_t total_vertices);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace lrcc

@@ -1,0 +1,483 @@
+// Runtime of liblrcc.so: per-stream workspaces, the plan table, graph
+// capture/caching and the extern "C" entry points declared in lrcc.h.
+#include <algorithm>
+#include <atomic>
+#include <cstddef>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrcc {
+
+namespace {
+
+std::mutex g_mu;
+std::atomic<int> g_timing{0};
+const char* const kPhaseNames[PH_COUNT] = {
+    "rs_select0", "rs_walk0", "rs_select", "rs_walk", "rs_final", "rs_expand", "rs_expand0", "lr_small",
+    "wy_pack", "wy_jump", "wy_final", "cc_init", "cc_loop", "cc_hook", "cc_shortcut",
+    "lr_batch", "cc_batch", "batch_prep"};
+std::map<std::pair<int, cudaStream_t>, Ctx*> g_ctx;
+std::mutex g_plan_mu;
+bool g_plan_init = false;
+Plan g_plan[6][33];
+
+int log2_ceil(int64_t n) {
+    int l = 0;
+    while (l < 32 && (int64_t(1) << l) < n) ++l;
+    return l;
+}
+
+void init_plans_locked() {
+    if (g_plan_init) return;
+    for (int k = 0; k < 6; ++k)
+        for (int l = 0; l <= 32; ++l) g_plan[k][l] = Plan{};
+    g_plan_init = true;
+}
+
+// Zero every control field except the sticky status word.
+void reset_ctl(Ctx* c, cudaStream_t s) {
+    cudaMemsetAsync(reinterpret_cast<char*>(c->ctl) + offsetof(DevCtl, flag), 0,
+                    sizeof(DevCtl) - offsetof(DevCtl, flag), s);
+}
+
+void drop_graphs(Ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+// Launch the work `rec` records, through a cached graph unless disabled.
+lrcc_status launch_recorded(Ctx* c, const Plan& p, std::vector<uint64_t> key,
+                            const std::function<lrcc_status(cudaStream_t)>& rec) {
+    if (p.use_graphs == 2 || timing_enabled()) return rec(c->stream);
+    key.push_back(reinterpret_cast<uint64_t>(c->ws));
+    GraphEntry* e = nullptr;
+    for (auto& ge : c->graphs)
+        if (ge.key == key) e = &ge;
+    if (!e) {
+        if (cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return LRCC_ERR_CUDA;
+        lrcc_status st = rec(c->capture);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c->capture, &g);
+        if (st == LRCC_OK && ce != cudaSuccess) st = LRCC_ERR_CUDA;
+        cudaGraphExec_t ex = nullptr;
+        if (st == LRCC_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) st = LRCC_ERR_CUDA;
+        if (g) cudaGraphDestroy(g);
+        if (st != LRCC_OK) {
+            cudaGetLastError();
+            return st;
+        }
+        if (c->graphs.size() >= 16) {
+            auto it = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                       [](const GraphEntry& a, const GraphEntry& b) {
+                                           return a.last_use < b.last_use;
+                                       });
+            cudaGraphExecDestroy(it->exec);
+            c->graphs.erase(it);
+        }
+        c->graphs.push_back(GraphEntry{std::move(key), ex, 0});
+        e = &c->graphs.back();
+    }
+    e->last_use = ++c->tick;
+    return cuda_status(cudaGraphLaunch(e->exec, c->stream));
+}
+
+std::vector<uint64_t> plan_key(const Plan& p) {
+    return {(uint64_t)p.rs_spacing0, (uint64_t)p.rs_spacing, (uint64_t)p.rs_small, (uint64_t)p.rs_chains,
+            (uint64_t)p.cc_hook, (uint64_t)p.cc_max_rounds, p.seed};
+}
+
+}  // namespace
+
+lrcc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LRCC_OK : LRCC_ERR_CUDA; }
+
+bool timing_enabled() { return g_timing.load(std::memory_order_relaxed) != 0; }
+
+namespace {
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+cudaEvent_t next_event(Ctx* c, size_t* idx) {
+    if (c->events_used == c->events.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->events.push_back(e);
+    }
+    *idx = c->events_used++;
+    return c->events[*idx];
+}
+}  // namespace
+
+void phase_begin(Ctx* c, cudaStream_t s) {
+    if (!timing_enabled() || capturing(s)) return;
+    size_t i = 0;
+    cudaEvent_t e = next_event(c, &i);
+    if (e && cudaEventRecord(e, s) == cudaSuccess) c->cur_begin = i;
+}
+
+void phase_end(Ctx* c, cudaStream_t s, int phase) {
+    if (!timing_enabled() || capturing(s)) return;
+    size_t i = 0;
+    cudaEvent_t e = next_event(c, &i);
+    if (e && cudaEventRecord(e, s) == cudaSuccess) c->recs.push_back(Ctx::Rec{phase, c->cur_begin, i});
+}
+
+Plan plan_for(int kind, int64_t n) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    init_plans_locked();
+    const int k = (kind == KIND_LR_WYLLIE) ? KIND_LR : kind;
+    return g_plan[std::min(std::max(k, 0), 5)][log2_ceil(std::max<int64_t>(n, 1))];
+}
+
+int persistent_grid(Ctx* c, const void* kernel, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(c->device, kernel);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int g = per_sm * c->sms;
+    cache[key] = g;
+    return g;
+}
+
+lrcc_status ctx_for(void* stream, Ctx** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LRCC_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(dev, s);
+    auto it = g_ctx.find(key);
+    if (it != g_ctx.end()) {
+        *out = it->second;
+        return LRCC_OK;
+    }
+    Ctx* c = new Ctx();
+    c->device = dev;
+    c->stream = s;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return LRCC_ERR_CUDA;
+    }
+    if (cudaMalloc(&c->ctl, sizeof(DevCtl)) != cudaSuccess) {
+        cudaStreamDestroy(c->capture);
+        delete c;
+        return LRCC_ERR_NOMEM;
+    }
+    if (cudaMemset(c->ctl, 0, sizeof(DevCtl)) != cudaSuccess) {
+        cudaFree(c->ctl);
+        cudaStreamDestroy(c->capture);
+        delete c;
+        return LRCC_ERR_CUDA;
+    }
+    g_ctx[key] = c;
+    *out = c;
+    return LRCC_OK;
+}
+
+lrcc_status ensure_ws(Ctx* c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return LRCC_OK;
+    const size_t old = c->ws_bytes;
+    // the old workspace may still be in use by queued work on this stream
+    if (c->ws) {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LRCC_ERR_CUDA;
+        drop_graphs(c);
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    const size_t want = std::max(bytes, old + old / 4);
+    if (cudaMalloc(&c->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->ws = nullptr;
+            return LRCC_ERR_NOMEM;
+        }
+        c->ws_bytes = bytes;
+        return LRCC_OK;
+    }
+    c->ws_bytes = want;
+    return LRCC_OK;
+}
+
+}  // namespace lrcc
+
+using namespace lrcc;
+
+extern "C" {
+
+const char* lrcc_status_str(int status) {
+    switch (status) {
+        case LRCC_OK: return "ok";
+        case LRCC_ERR_ARG: return "bad argument";
+        case LRCC_ERR_NOMEM: return "out of device memory";
+        case LRCC_ERR_CUDA: return "CUDA runtime error";
+        case LRCC_ERR_INVALID_INPUT: return "invalid input (not a single list, or an id out of range)";
+        case LRCC_ERR_NOT_CONVERGED: return "component loop reached its round cap";
+        case LRCC_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int lrcc_version(void) { return 100; }
+
+lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Plan p = plan_for(KIND_LR, n);
+    const RsLayout L = rs_layout(n, p);
+    if (n > p.rs_small) {
+        st = ensure_ws(c, L.bytes);
+        if (st != LRCC_OK) return st;
+    }
+    std::vector<uint64_t> key = {(uint64_t)KIND_LR, (uint64_t)succ, (uint64_t)n, (uint64_t)head, (uint64_t)rank};
+    const auto pk = plan_key(p);
+    key.insert(key.end(), pk.begin(), pk.end());
+    st = launch_recorded(c, p, key, [&](cudaStream_t s) {
+        reset_ctl(c, s);
+        return lr_enqueue_rs(c, s, succ, n, head, rank, p, L);
+    });
+    c->last_kind = KIND_LR;
+    c->last_levels = n > p.rs_small ? L.levels : 0;
+    for (int l = 0; l < MAX_LEVELS; ++l) c->last_splitter_cap[l] = l < L.levels ? L.size[l + 1] : 0;
+    return st;
+}
+
+lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Plan p = plan_for(KIND_LR_WYLLIE, n);
+    if (n > p.rs_small) {
+        st = ensure_ws(c, lr_wyllie_ws(n, p));
+        if (st != LRCC_OK) return st;
+    }
+    std::vector<uint64_t> key = {(uint64_t)KIND_LR_WYLLIE, (uint64_t)succ, (uint64_t)n, (uint64_t)head,
+                                 (uint64_t)rank, (uint64_t)p.rs_small};
+    st = launch_recorded(c, p, key, [&](cudaStream_t s) {
+        reset_ctl(c, s);
+        return lr_enqueue_wyllie(c, s, succ, n, head, rank, p);
+    });
+    c->last_kind = KIND_LR_WYLLIE;
+    c->last_levels = 0;
+    return st;
+}
+
+lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label,
+                     void* stream) {
+    if (n < 0 || m < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return m == 0 ? LRCC_OK : LRCC_ERR_ARG;
+    if (!label || (m > 0 && (!src || !dst))) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Plan p = plan_for(KIND_CC, n);
+    reset_ctl(c, c->stream);
+    st = cc_run(c, src, dst, m, n, label, p);
+    c->last_kind = KIND_CC;
+    return st;
+}
+
+lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
+                            int64_t num_lists, int32_t* rank, void* stream) {
+    if (num_lists < 0) return LRCC_ERR_ARG;
+    if (num_lists == 0) return LRCC_OK;
+    if (!node_off || !heads) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Plan p = plan_for(KIND_LR_BATCH, 0);
+    reset_ctl(c, c->stream);
+    st = lr_batched_run(c, succ, node_off, heads, num_lists, rank, p);
+    c->last_kind = KIND_LR_BATCH;
+    return st;
+}
+
+lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
+                             const int64_t* vert_off, int64_t num_graphs, int32_t* label, void* stream) {
+    if (num_graphs < 0) return LRCC_ERR_ARG;
+    if (num_graphs == 0) return LRCC_OK;
+    if (!edge_off || !vert_off) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Plan p = plan_for(KIND_CC_BATCH, 0);
+    reset_ctl(c, c->stream);
+    st = cc_batched_run(c, src, dst, edge_off, vert_off, num_graphs, label, p);
+    c->last_kind = KIND_CC_BATCH;
+    return st;
+}
+
+lrcc_status lrcc_last_status(void* stream) {
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LRCC_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LRCC_ERR_CUDA;
+    if (v != 0 && cudaMemset(&c->ctl->status, 0, sizeof(int)) != cudaSuccess) return LRCC_ERR_CUDA;
+    return static_cast<lrcc_status>(v);
+}
+
+lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out) {
+    if (!out) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LRCC_ERR_CUDA;
+    DevCtl h;
+    if (cudaMemcpy(&h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost) != cudaSuccess) return LRCC_ERR_CUDA;
+    std::memset(out, 0, sizeof(*out));
+    out->kind = c->last_kind;
+    out->levels = c->last_levels;
+    for (int l = 0; l < c->last_levels && l < 8; ++l)
+        out->splitters[l] = std::min<int64_t>(1 + (int64_t)h.spl_count[l], c->last_splitter_cap[l]);
+    out->rounds = h.rounds;
+    out->jump_rounds = h.jump_rounds;
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* plan) {
+    if (!plan || kind < 1 || kind > 5 || log2_lo < 0 || log2_hi > 32 || log2_lo > log2_hi) return LRCC_ERR_ARG;
+    if (plan->rs_small < 0 || plan->rs_small > 16384 || plan->rs_spacing0 < 0 || plan->rs_spacing < 0 ||
+        (plan->rs_spacing0 > 0 && plan->rs_spacing0 < 2) || (plan->rs_spacing > 0 && plan->rs_spacing < 2) ||
+        (plan->rs_small > 0 && plan->rs_small < 1024) || plan->rs_chains < 0 || plan->rs_chains > 4 ||
+        plan->cc_hook < 0 || plan->cc_hook > 2 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
+        plan->use_graphs > 2)
+        return LRCC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    init_plans_locked();
+    for (int l = log2_lo; l <= log2_hi; ++l) {
+        Plan& p = g_plan[kind][l];
+        if (plan->rs_spacing0) p.rs_spacing0 = plan->rs_spacing0;
+        if (plan->rs_spacing) p.rs_spacing = plan->rs_spacing;
+        if (plan->rs_small) p.rs_small = plan->rs_small;
+        if (plan->rs_chains) p.rs_chains = plan->rs_chains;
+        if (plan->cc_hook) p.cc_hook = plan->cc_hook;
+        if (plan->cc_max_rounds) p.cc_max_rounds = plan->cc_max_rounds < 0 ? 0 : plan->cc_max_rounds;
+        if (plan->use_graphs) p.use_graphs = plan->use_graphs;
+        if (plan->seed) p.seed = plan->seed;
+    }
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_get_plan(int kind, int64_t n, lrcc_plan* out) {
+    if (!out || kind < 1 || kind > 5) return LRCC_ERR_ARG;
+    const Plan p = plan_for(kind, n);
+    std::memset(out, 0, sizeof(*out));
+    out->rs_spacing0 = p.rs_spacing0;
+    out->rs_spacing = p.rs_spacing;
+    out->rs_small = p.rs_small;
+    out->rs_chains = p.rs_chains;
+    out->cc_hook = p.cc_hook;
+    out->cc_max_rounds = p.cc_max_rounds;
+    out->use_graphs = p.use_graphs;
+    out->seed = p.seed;
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_set_timing(int enable) {
+    g_timing.store(enable ? 1 : 0);
+    return LRCC_OK;
+}
+
+int lrcc_phase_count(void) { return PH_COUNT; }
+
+const char* lrcc_phase_name(int phase) {
+    return (phase >= 0 && phase < PH_COUNT) ? kPhaseNames[phase] : "unknown";
+}
+
+lrcc_status lrcc_phase_times(void* stream, double* ms_total, int64_t* launches) {
+    if (!ms_total || !launches) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LRCC_ERR_CUDA;
+    for (const auto& r : c->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->events[r.a], c->events[r.b]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        ms_total[r.phase] += ms;
+        launches[r.phase] += 1;
+    }
+    c->recs.clear();
+    c->events_used = 0;
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_release(void* stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LRCC_ERR_CUDA;
+    Ctx* c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ctx.find(std::make_pair(dev, static_cast<cudaStream_t>(stream)));
+        if (it == g_ctx.end()) return LRCC_OK;
+        c = it->second;
+        g_ctx.erase(it);
+    }
+    cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (auto e : c->events) cudaEventDestroy(e);
+    if (c->ws) cudaFree(c->ws);
+    cudaFree(c->ctl);
+    cudaStreamDestroy(c->capture);
+    delete c;
+    return LRCC_OK;
+}
+
+int64_t lrcc_workspace_bytes(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int64_t t = 0;
+    for (auto& kv : g_ctx) t += (int64_t)kv.second->ws_bytes + (int64_t)sizeof(DevCtl);
+    return t;
+}
+
+int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
+    (void)m;
+    if (n < 0) return -1;
+    const Plan p = plan_for(kind, n);
+    switch (kind) {
+        case KIND_LR: return n > p.rs_small ? (int64_t)rs_layout(n, p).bytes : 0;
+        case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
+        case KIND_CC: return 0;
+        case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n);
+        case KIND_CC_BATCH: return (int64_t)cc_batched_ws(n);
+        default: return -1;
+    }
+}
+
+}  // extern "C"

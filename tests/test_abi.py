@@ -1,0 +1,87 @@
+"""The C-ABI library loads and exports every function include/lrcc.h declares
+(no GPU needed; no compute call is made)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1002_4482_gb300 as lrcc
+from paper_1002_4482_gb300 import _build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lrcc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)
+    skip = {"if", "for", "while", "return", "sizeof", "defined"}
+    return sorted({n for n in names if n not in skip and not n.startswith("__")})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ctypes.CDLL(_build.OUT)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("lr_rank", "lr_rank_wyllie", "cc_label", "lr_rank_batched", "cc_label_batched",
+              "lrcc_last_status"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"liblrcc.so does not export {name}"
+
+
+def test_binding_names_match_header():
+    assert set(lrcc.SYMBOLS) == set(declared_functions())
+
+
+def test_status_strings(lib):
+    lrcc.load()
+    assert lrcc.status_str(0) == "ok"
+    assert "invalid input" in lrcc.status_str(4)
+    assert lrcc.status_str(99) == "unknown status"
+    assert lrcc.load().lrcc_version() == 100
+
+
+def test_host_side_argument_errors_need_no_gpu(lib):
+    # rejected before any CUDA call: negative size, head out of range, NULL pointers
+    L = lrcc.load()
+    assert L.lr_rank(None, -1, 0, None, None) == lrcc.ERR_ARG
+    assert L.lr_rank(None, 0, 0, None, None) == lrcc.OK
+    assert L.lr_rank(ctypes.c_void_p(16), 10, 10, ctypes.c_void_p(16), None) == lrcc.ERR_ARG
+    assert L.lr_rank(None, 10, 0, None, None) == lrcc.ERR_ARG
+    assert L.lr_rank_wyllie(None, 5, -1, None, None) == lrcc.ERR_ARG
+    assert L.cc_label(None, None, 0, 0, None, None) == lrcc.OK
+    assert L.cc_label(None, None, 5, 0, None, None) == lrcc.ERR_ARG
+    assert L.cc_label(None, None, 0, 5, None, None) == lrcc.ERR_ARG
+    assert L.lr_rank_batched(None, None, None, 0, None, None) == lrcc.OK
+    assert L.cc_label_batched(None, None, None, None, -1, None, None) == lrcc.ERR_ARG
+
+
+def test_plan_table_roundtrip(lib):
+    before = lrcc.get_plan(lrcc.KIND_LR, 1 << 20)
+    lrcc.set_plan(lrcc.KIND_LR, 20, 20, rs_spacing0=64)
+    assert lrcc.get_plan(lrcc.KIND_LR, 1 << 20)["rs_spacing0"] == 64
+    assert lrcc.get_plan(lrcc.KIND_LR, 1 << 21)["rs_spacing0"] == before["rs_spacing0"]
+    lrcc.set_plan(lrcc.KIND_LR, 20, 20, rs_spacing0=before["rs_spacing0"])
+    with pytest.raises(lrcc.LrccError):
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_small=100000)
+    with pytest.raises(lrcc.LrccError):
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=3)
+
+
+def test_workspace_query(lib):
+    L = lrcc.load()
+    assert L.lrcc_workspace_query(lrcc.KIND_LR, 1000, 0) == 0          # one block, no workspace
+    big = L.lrcc_workspace_query(lrcc.KIND_LR, 1 << 28, 0)
+    assert 8 * (1 << 28) <= big < 10 * (1 << 28)                        # 8-byte walk words + small levels
+    assert L.lrcc_workspace_query(lrcc.KIND_LR_WYLLIE, 1 << 20, 0) == 16 * (1 << 20)

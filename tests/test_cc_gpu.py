@@ -1,0 +1,135 @@
+"""Connected-components parity: the CUDA path (through the C ABI) against the
+oracle, element by element, bit-exact (min-id labels are unique)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1002_4482_gb300 as lrcc
+from gen import workloads
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def _run(src, dst, n):
+    s = torch.from_numpy(np.ascontiguousarray(src, np.int32)).to(DEV)
+    d = torch.from_numpy(np.ascontiguousarray(dst, np.int32)).to(DEV)
+    lab = lrcc.cc_label(s, d, n)
+    lrcc.check()
+    return lab.cpu().numpy()
+
+
+@pytest.fixture(params=[1, 2], ids=["hook-once", "hook-relink"])
+def hook(request):
+    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 20)["cc_hook"]
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=request.param)
+    yield request.param
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=base)
+
+
+@pytest.mark.parametrize("n,m", [(1, 0), (1, 1), (5, 0), (10, 3), (33, 40), (1000, 500), (1000, 3000),
+                                 (1 << 14, 1 << 15), (100_003, 150_001)])
+def test_er_matches_oracle(hook, n, m):
+    for seed in (1, 2):
+        src, dst = gen.er(n, m, seed)
+        assert np.array_equal(_run(src, dst, n), oracle.cc_bfs(src, dst, n))
+
+
+def test_er_2p20_2p22_matches_oracle(hook):
+    src, dst, n = workloads.cc_er(20, 22)
+    lab = _run(src, dst, n)
+    assert np.array_equal(lab, oracle.cc_uf(src, dst, n))
+    st = lrcc.last_stats()
+    assert st["rounds"] >= 2
+
+
+def test_rmat_scale16_matches_oracle(hook):
+    src, dst, n = workloads.cc_rmat(16, 16)
+    assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
+
+
+@pytest.mark.parametrize("k,seg,cycle", [(1, 100_000, False), (1, 99_999, True), (64, 1000, True),
+                                         (3000, 7, False)])
+def test_paths_and_cycles(hook, k, seg, cycle):
+    # long paths are the slow case for hooking (Sec. 4: lists take many rounds)
+    n = k * seg
+    relabel = gen.permutation(n, 21)
+    ids = relabel.reshape(k, seg)
+    src = ids[:, :-1].ravel()
+    dst = ids[:, 1:].ravel()
+    if cycle:
+        src = np.concatenate([src, ids[:, -1]])
+        dst = np.concatenate([dst, ids[:, 0]])
+    order = gen.permutation(len(src), 22)
+    lab = _run(src[order], dst[order], n)
+    assert np.array_equal(lab, oracle.cc_uf(src, dst, n))
+    assert len(np.unique(lab)) == k
+
+
+def test_self_loops_duplicates_isolated(hook):
+    src = np.array([3, 3, 3, 7, 7, 1], np.int32)
+    dst = np.array([3, 5, 5, 7, 5, 1], np.int32)
+    assert _run(src, dst, 9).tolist() == [0, 1, 2, 3, 4, 3, 6, 3, 8]
+
+
+def test_graphs_off_and_repeated(hook):
+    src, dst = gen.er(200_000, 300_000, 3)
+    expect = oracle.cc_uf(src, dst, 200_000)
+    for _ in range(5):
+        assert np.array_equal(_run(src, dst, 200_000), expect)
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=2)
+    try:
+        assert np.array_equal(_run(src, dst, 200_000), expect)
+    finally:
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=1)
+
+
+def test_unaligned_views():
+    src, dst = gen.er(10_001, 20_003, 4)
+    s = torch.zeros(20_005, dtype=torch.int32, device=DEV)
+    d = torch.zeros(20_005, dtype=torch.int32, device=DEV)
+    s[1:20_004] = torch.from_numpy(src).to(DEV)
+    d[1:20_004] = torch.from_numpy(dst).to(DEV)
+    out = torch.zeros(10_003, dtype=torch.int32, device=DEV)
+    lrcc.cc_label(s[1:20_004], d[1:20_004], 10_001, out=out[1:10_002])
+    lrcc.check()
+    assert np.array_equal(out[1:10_002].cpu().numpy(), oracle.cc_uf(src, dst, 10_001))
+
+
+def test_out_of_range_edge_is_reported():
+    src = np.array([0, 1, 2], np.int32)
+    dst = np.array([1, 2, 9], np.int32)
+    s, d = torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV)
+    lrcc.cc_label(s, d, 5)
+    assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+    assert _run(src[:2], dst[:2], 5).tolist() == [0, 0, 0, 3, 4]
+
+
+def test_round_cap_is_reported():
+    # with a cap of one pass, any graph whose first pass joins two trees must
+    # stop with NOT_CONVERGED; the default cap then labels it correctly
+    src, dst = gen.er(5000, 4000, 5)
+    s, d = torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV)
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_max_rounds=1)
+    try:
+        lrcc.cc_label(s, d, 5000)
+        st = lrcc.last_status()
+    finally:
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_max_rounds=-1)
+    assert st == lrcc.ERR_NOT_CONVERGED
+    assert lrcc.get_plan(lrcc.KIND_CC, 5000)["cc_max_rounds"] == 0
+    assert np.array_equal(_run(src, dst, 5000), oracle.cc_uf(src, dst, 5000))
+
+
+@pytest.mark.slow
+def test_full_size_rmat_scale24(hook):
+    # the bench workload: R-MAT 2^24 vertices, 2^28 edges, against the union-find oracle
+    src, dst, n = workloads.cc_rmat(24, 16)
+    lab = _run(src, dst, n)
+    pins.cc_invariants(src[: 1 << 24], dst[: 1 << 24], n, lab)
+    assert np.array_equal(lab, oracle.cc_uf(src, dst, n))

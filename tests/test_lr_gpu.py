@@ -1,0 +1,164 @@
+"""List-ranking parity: the CUDA path (through the C ABI) against the oracle,
+element by element, bit-exact (integers; tolerance 0)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1002_4482_gb300 as lrcc
+from gen import workloads
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+FNS = {"rs": lrcc.lr_rank, "wyllie": lrcc.lr_rank_wyllie}
+
+
+def _run(fn, succ, head):
+    t = torch.from_numpy(np.ascontiguousarray(succ)).to(DEV)
+    r = FNS[fn](t, head)
+    lrcc.check()
+    return r.cpu().numpy()
+
+
+@pytest.mark.parametrize("fn", ["rs", "wyllie"])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1000, 8191, 8192, 8193, 65539, 200003])
+def test_random_list_matches_oracle(fn, n):
+    for seed in (1, 2):
+        succ, head = gen.list_random(n, seed)
+        assert np.array_equal(_run(fn, succ, head), oracle.lr_rank(succ, head))
+
+
+@pytest.mark.parametrize("fn", ["rs", "wyllie"])
+def test_list_2p20_matches_oracle(fn):
+    succ, head = workloads.lr_random(20)
+    assert np.array_equal(_run(fn, succ, head), oracle.lr_rank(succ, head))
+
+
+@pytest.mark.parametrize("fn", ["rs", "wyllie"])
+def test_ordered_and_reversed_layouts(fn):
+    n = 100_003
+    succ, head = gen.list_ordered(n)
+    assert np.array_equal(_run(fn, succ, head), np.arange(n - 1, -1, -1))
+    rev = np.arange(-1, n - 1, dtype=np.int32)   # succ[i] = i - 1, head n-1
+    assert np.array_equal(_run(fn, rev, n - 1), np.arange(n))
+
+
+@pytest.mark.parametrize("fn", ["rs", "wyllie"])
+def test_selfloop_tail_convention(fn):
+    succ, head = gen.list_random(50_000, 3)
+    tail = int(np.flatnonzero(succ == -1)[0])
+    s2 = succ.copy()
+    s2[tail] = tail
+    assert np.array_equal(_run(fn, s2, head), oracle.lr_rank(succ, head))
+
+
+def test_result_independent_of_splitters():
+    succ, head = gen.list_random(300_000, 4)
+    expect = oracle.lr_rank(succ, head)
+    base = lrcc.get_plan(lrcc.KIND_LR, 300_000)
+    try:
+        for seed in (1, 2, 3, 99, 12345):
+            for spacing0, spacing, chains, small in ((32, 16, 2, 8192), (4, 4, 1, 1024), (256, 64, 4, 16384),
+                                                     (2, 2, 2, 1024)):
+                lrcc.set_plan(lrcc.KIND_LR, 0, 32, seed=seed, rs_spacing0=spacing0, rs_spacing=spacing,
+                              rs_chains=chains, rs_small=small)
+                assert np.array_equal(_run("rs", succ, head), expect), (seed, spacing0, spacing, chains)
+    finally:
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, **{k: v for k, v in base.items()})
+
+
+def test_without_graphs_and_repeated():
+    succ, head = gen.list_random(500_000, 5)
+    expect = oracle.lr_rank(succ, head)
+    t = torch.from_numpy(succ).to(DEV)
+    for _ in range(10):
+        assert np.array_equal(lrcc.lr_rank(t, head).cpu().numpy(), expect)
+    lrcc.set_plan(lrcc.KIND_LR, 0, 32, use_graphs=2)
+    lrcc.set_plan(lrcc.KIND_LR_WYLLIE, 0, 32, use_graphs=2)
+    try:
+        assert np.array_equal(lrcc.lr_rank(t, head).cpu().numpy(), expect)
+        assert np.array_equal(lrcc.lr_rank_wyllie(t, head).cpu().numpy(), expect)
+    finally:
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, use_graphs=1)
+        lrcc.set_plan(lrcc.KIND_LR_WYLLIE, 0, 32, use_graphs=1)
+    lrcc.check()
+
+
+@pytest.mark.parametrize("fn", ["rs", "wyllie"])
+def test_unaligned_views(fn):
+    # views that start one element into an allocation take the scalar paths
+    succ, head = gen.list_random(70_001, 6)
+    buf = torch.zeros(70_003, dtype=torch.int32, device=DEV)
+    buf[1:70_002] = torch.from_numpy(succ).to(DEV)
+    out = torch.zeros(70_003, dtype=torch.int32, device=DEV)
+    FNS[fn](buf[1:70_002], head, out=out[1:70_002])
+    lrcc.check()
+    assert np.array_equal(out[1:70_002].cpu().numpy(), oracle.lr_rank(succ, head))
+
+
+@pytest.mark.parametrize("fn", ["rs", "wyllie"])
+@pytest.mark.parametrize("case", ["cycle", "two_lists", "out_of_range", "shared_successor", "big_cycle"])
+def test_invalid_inputs_are_reported(fn, case):
+    n = 20_000
+    succ, head = gen.list_random(n, 7)
+    succ = succ.copy()
+    tail = int(np.flatnonzero(succ == -1)[0])
+    if case == "cycle":
+        succ[tail] = head                          # the whole list becomes a cycle
+    elif case == "two_lists":
+        succ[succ[head]] = -1                      # cut after the second element
+    elif case == "out_of_range":
+        succ[tail] = n + 5
+    elif case == "shared_successor":
+        succ[tail] = succ[head]                    # tail points back into the list
+    elif case == "big_cycle":
+        mid = succ[succ[succ[head]]]
+        succ[tail] = mid
+    with pytest.raises(oracle.OracleInvalid):
+        oracle.lr_rank(succ, head)
+    t = torch.from_numpy(succ).to(DEV)
+    FNS[fn](t, head)
+    assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+    # the stream and the library stay usable
+    good, h = gen.list_random(n, 8)
+    assert np.array_equal(_run(fn, good, h), oracle.lr_rank(good, h))
+
+
+def test_host_argument_errors():
+    t = torch.zeros(10, dtype=torch.int32, device=DEV)
+    with pytest.raises(lrcc.LrccError):
+        lrcc.lr_rank(t, 10)
+    with pytest.raises(lrcc.LrccError):
+        lrcc.lr_rank(t, -1)
+    assert lrcc.lr_rank(torch.zeros(0, dtype=torch.int32, device=DEV), 0).numel() == 0
+
+
+def test_stats_report_levels():
+    succ, head = gen.list_random(1 << 22, 9)
+    _run("rs", succ, head)
+    st = lrcc.last_stats()
+    assert st["levels"] >= 1 and st["splitters"][0] > 1
+    assert st["splitters"] == sorted(st["splitters"], reverse=True)
+
+
+@pytest.mark.slow
+def test_full_size_2p28_random_and_ordered():
+    # the bench workload: n = 2^28 in random layout; checked exactly against the
+    # generator's closed form rank[perm[k]] = n-1-k and the invariants
+    n = 1 << 28
+    succ, head, perm = workloads.lr_random(28, with_perm=True)
+    t = torch.from_numpy(succ).to(DEV)
+    rank = lrcc.lr_rank(t, head)
+    lrcc.check()
+    r = rank.cpu().numpy()
+    assert np.array_equal(r[perm], np.arange(n - 1, -1, -1, dtype=np.int32))
+    pins.lr_sample(succ, head, r, 1 << 22, 0)
+    del t, rank
+    succ, head = workloads.lr_ordered(28)
+    rank = lrcc.lr_rank(torch.from_numpy(succ).to(DEV), head)
+    lrcc.check()
+    assert np.array_equal(rank.cpu().numpy(), np.arange(n - 1, -1, -1, dtype=np.int32))

@@ -141,10 +141,14 @@ typedef struct lrcc_plan {
     int32_t rs_spacing;      /* mean sublist length at deeper levels */
     int32_t rs_small;        /* lists of at most this many elements are ranked by one block */
     int32_t rs_chains;       /* sublist walks interleaved per thread: 1, 2 or 4 */
-    int32_t cc_hook;         /* 1 = one atomicMin per edge and pass, 2 = re-link until joined */
+    int32_t cc_hook;         /* 1 = one atomicMin per edge and pass, 2 = re-link until joined,
+                                3 = rule 1 in the first pass, rule 2 after */
     int32_t cc_max_rounds;   /* cap on hook passes (-1 = back to the automatic cap) */
     int32_t use_graphs;      /* 1 = replay captured CUDA graphs, 2 = plain launches */
-    int32_t reserved;
+    int32_t rs_level0;       /* first ruling-set level: 1 = the walk rewrites 8-byte words in
+                                place; 2 = the walk only reads succ and writes what it visits
+                                as 32-byte chunks, which are turned into ranks by a scatter
+                                into id-range buckets and a placement pass */
     uint64_t seed;           /* splitter seed (results do not depend on it) */
 } lrcc_plan;
 
@@ -167,6 +171,18 @@ lrcc_status lrcc_set_timing(int enable);
 int lrcc_phase_count(void);
 const char* lrcc_phase_name(int phase);
 lrcc_status lrcc_phase_times(void* stream, double* ms_total, int64_t* launches);
+
+/*
+ * L2 fetch granularity of the current device's context, in bytes (32, 64 or
+ * 128; 0 = leave the driver's default). Random 4- and 8-byte gathers over
+ * arrays larger than L2 (the sublist walk, the hook's parent reads) move a
+ * whole fetch unit from HBM per access, so a 32-byte unit cuts their DRAM
+ * traffic. It is a hint the driver may clamp, it applies to every kernel of
+ * the process on that device (not only this library's), and it ends with the
+ * process. lrcc_get_l2_fetch_granularity returns the current value or -1.
+ */
+lrcc_status lrcc_set_l2_fetch_granularity(int bytes);
+int lrcc_get_l2_fetch_granularity(void);
 
 /* Frees the workspace and cached graphs of `stream` (waits for it first). */
 lrcc_status lrcc_release(void* stream);

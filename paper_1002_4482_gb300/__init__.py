@@ -33,7 +33,7 @@ SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "cc_l
            "lr_rank_batched", "cc_label_batched", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
-           "lrcc_phase_times")
+           "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity")
 
 
 class LrccError(RuntimeError):
@@ -52,7 +52,7 @@ class Plan(ctypes.Structure):
     _fields_ = [("rs_spacing0", ctypes.c_int32), ("rs_spacing", ctypes.c_int32),
                 ("rs_small", ctypes.c_int32), ("rs_chains", ctypes.c_int32),
                 ("cc_hook", ctypes.c_int32), ("cc_max_rounds", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("rs_level0", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -91,9 +91,11 @@ def load() -> ctypes.CDLL:
         lib.lrcc_phase_name.argtypes = [i]
         lib.lrcc_phase_name.restype = ctypes.c_char_p
         lib.lrcc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        lib.lrcc_set_l2_fetch_granularity.argtypes = [i]
+        lib.lrcc_get_l2_fetch_granularity.restype = i
         for f in ("lr_rank", "lr_rank_wyllie", "cc_label", "lr_rank_batched", "cc_label_batched",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
-                  "lrcc_release", "lrcc_set_timing", "lrcc_phase_times"):
+                  "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
             getattr(lib, f).restype = i
         _lib = lib
         return lib
@@ -227,7 +229,7 @@ def set_plan(kind: int, log2_lo: int = 0, log2_hi: int = 32, **fields) -> None:
 def get_plan(kind: int, n: int) -> dict:
     p = Plan()
     _call(load().lrcc_get_plan(kind, n, ctypes.byref(p)), "lrcc_get_plan")
-    return {f: getattr(p, f) for f, _ in Plan._fields_ if f != "reserved"}
+    return {f: getattr(p, f) for f, _ in Plan._fields_}
 
 
 def release(stream=None) -> None:
@@ -255,3 +257,12 @@ def phase_times(stream=None) -> dict:
     cnt = (ctypes.c_int64 * k)()
     _call(lib.lrcc_phase_times(_stream(stream), ms, cnt), "lrcc_phase_times")
     return {lib.lrcc_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(k) if cnt[i]}
+
+
+def set_l2_fetch_granularity(nbytes: int) -> None:
+    """L2 fetch unit (32/64/128 B) of the current device's context; affects every kernel."""
+    _call(load().lrcc_set_l2_fetch_granularity(int(nbytes)), "lrcc_set_l2_fetch_granularity")
+
+
+def get_l2_fetch_granularity() -> int:
+    return int(load().lrcc_get_l2_fetch_granularity())

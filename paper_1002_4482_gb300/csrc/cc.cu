@@ -19,7 +19,8 @@
 // Shiloach-Vishkin round structure; 2 = when the atomicMin finds that the
 // larger root was linked meanwhile, keep joining (old parent, smaller root)
 // until one link lands, so each pass joins every edge and the next pass only
-// confirms. Both give the same labels.
+// confirms; 3 = rule 1 in the first pass, rule 2 after it. All give the same
+// labels.
 #include <algorithm>
 
 #include "common.cuh"
@@ -49,40 +50,74 @@ __global__ void __launch_bounds__(BLOCK) cc_init(int32_t* __restrict__ parent, i
 
 // Follow parents to a root. Every link goes to a smaller id, so the walk
 // ends within n steps on any state the kernels can produce.
-__device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t x) {
+__device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t x, uint64_t keep) {
     for (;;) {
-        const int32_t p = ld_cg(parent + x);
+        const int32_t p = ld_cg_hint(parent + x, keep);
         if (p == x) return x;
         x = p;
     }
 }
 
-template <int MODE>
-__device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b) {
+// Root of x with path halving: each visited element is re-pointed to its
+// grandparent. The store may race with an atomicMin on the same element;
+// either value is an ancestor, and a link that such a store replaces is
+// re-made by the thread whose atomicMin saw it (it goes on to join the old
+// parent with its smaller root), so no connection is lost.
+__device__ __forceinline__ int32_t find_root_halving(int32_t* parent, int32_t x, uint64_t keep) {
+    int32_t p = ld_cg_hint(parent + x, keep);
+    while (p != x) {
+        const int32_t g = ld_cg_hint(parent + p, keep);
+        if (g == p) return p;
+        parent[x] = g;
+        x = g;
+        p = ld_cg_hint(parent + x, keep);
+    }
+    return x;
+}
+
+// One edge whose endpoints currently have parents a and b.
+//  relink = false: a single atomicMin links the larger parent below the
+//                  smaller one (one Shiloach-Vishkin style hook);
+//  relink = true:  both ends are followed to their roots; when the atomicMin
+//                  finds the larger root already linked below `old` by
+//                  another thread, the join continues with (old, smaller
+//                  root), so the edge's endpoints share a tree when it returns.
+// Returns whether a link was written.
+__device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b, bool relink, uint64_t keep) {
     if (a == b) return false;
-    if constexpr (MODE == 1) {
-        atomicMin(parent + max(a, b), min(a, b));
+    if (!relink) {
+        // Read before the atomic: on hubs most hooks find the parent already
+        // at or below `lo`, and skipping those keeps same-address atomics
+        // from serialising in L2.
+        const int32_t hi = max(a, b), lo = min(a, b);
+        if (ld_cg_hint(parent + hi, keep) > lo) atomicMin(parent + hi, lo);
         return true;
-    } else {
+    }
+    bool linked = false;
     for (;;) {
-        a = find_root(parent, a);
-        b = find_root(parent, b);
-        if (a == b) return true;
+        a = find_root_halving(parent, a, keep);
+        b = find_root_halving(parent, b, keep);
+        if (a == b) return linked;
         const int32_t hi = max(a, b), lo = min(a, b);
         const int32_t old = atomicMin(parent + hi, lo);
+        linked = true;
         if (old == hi) return true;
         // hi had been linked below `old` by another thread: join old and lo
         a = old;
         b = lo;
     }
-    }
 }
 
-template <int MODE, bool VEC>
+// Hook pass. mode 1: single hooks every pass; mode 2: relink every pass;
+// mode 3: single hooks in the first pass (cheap while every tree is a
+// singleton), relink afterwards.
+template <bool VEC>
 __global__ void __launch_bounds__(BLOCK)
     cc_hook(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-            int32_t* parent, int64_t n, DevCtl* ctl) {
-    const uint64_t pol = policy_evict_first();
+            int32_t* parent, int64_t n, int mode, DevCtl* ctl) {
+    const uint64_t stream_pol = policy_evict_first();
+    const uint64_t keep = policy_evict_last();
+    const bool relink = mode == 2 || (mode == 3 && ctl->rounds > 0);
     const int64_t ngroups = (m + 3) >> 2;
     bool changed = false;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
@@ -90,15 +125,15 @@ __global__ void __launch_bounds__(BLOCK)
         const int64_t e0 = g * 4;
         int u[4], v[4];
         if (VEC && e0 + 3 < m) {
-            const int4 a = ld_stream_v4(src + e0, pol);
-            const int4 b = ld_stream_v4(dst + e0, pol);
+            const int4 a = ld_stream_v4(src + e0, stream_pol);
+            const int4 b = ld_stream_v4(dst + e0, stream_pol);
             u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
             v[0] = b.x; v[1] = b.y; v[2] = b.z; v[3] = b.w;
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                u[q] = e0 + q < m ? ld_stream(src + e0 + q, pol) : 0;
-                v[q] = e0 + q < m ? ld_stream(dst + e0 + q, pol) : 0;
+                u[q] = e0 + q < m ? ld_stream(src + e0 + q, stream_pol) : 0;
+                v[q] = e0 + q < m ? ld_stream(dst + e0 + q, stream_pol) : 0;
             }
         }
 #pragma unroll
@@ -111,11 +146,11 @@ __global__ void __launch_bounds__(BLOCK)
         int32_t a[4], b[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            a[q] = parent[u[q]];
-            b[q] = parent[v[q]];
+            a[q] = ld_hint(parent + u[q], keep);
+            b[q] = ld_hint(parent + v[q], keep);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) changed |= hook_pair<MODE>(parent, a[q], b[q]);
+        for (int q = 0; q < 4; ++q) changed |= hook_pair(parent, a[q], b[q], relink, keep);
     }
     if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) ctl->flag = 1;
 }
@@ -124,6 +159,7 @@ __global__ void __launch_bounds__(BLOCK)
 // this pass and every value read is an ancestor, so one pass suffices.
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n) {
+    const uint64_t keep = policy_evict_last();
     const int64_t ngroups = (n + 3) >> 2;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
          g += static_cast<int64_t>(gridDim.x) * BLOCK) {
@@ -135,7 +171,7 @@ __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (pp[q] != (int)(i0 + q)) {
-                    const int r = find_root(parent, pp[q]);
+                    const int r = find_root(parent, pp[q], keep);
                     ch |= r != pp[q];
                     pp[q] = r;
                 }
@@ -147,7 +183,7 @@ __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n)
                 if (v < n) {
                     const int p = parent[v];
                     if (p != v) {
-                        const int r = find_root(parent, p);
+                        const int r = find_root(parent, p, keep);
                         if (r != p) parent[v] = r;
                     }
                 }
@@ -200,20 +236,14 @@ struct CcArgs {
 lrcc_status enqueue_round(Ctx* c, cudaStream_t s, const CcArgs& a) {
     const bool ve = aligned16(a.src) && aligned16(a.dst);
     const bool vn = aligned16(a.label);
-    const void* hk = a.mode == 1 ? (ve ? (const void*)cc_hook<1, true> : (const void*)cc_hook<1, false>)
-                                 : (ve ? (const void*)cc_hook<2, true> : (const void*)cc_hook<2, false>);
+    const void* hk = ve ? (const void*)cc_hook<true> : (const void*)cc_hook<false>;
     const int64_t eg = (a.m + 3) / 4;
     if (eg > 0) {
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((eg + BLOCK - 1) / BLOCK,
                                                                   persistent_grid(c, hk, BLOCK)));
         phase_begin(c, s);
-        if (a.mode == 1) {
-            if (ve) cc_hook<1, true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
-            else cc_hook<1, false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
-        } else {
-            if (ve) cc_hook<2, true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
-            else cc_hook<2, false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, c->ctl);
-        }
+        if (ve) cc_hook<true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, c->ctl);
+        else cc_hook<false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, c->ctl);
         phase_end(c, s, PH_CC_HOOK);
     }
     const void* sk = vn ? (const void*)cc_shortcut<true> : (const void*)cc_shortcut<false>;
@@ -267,7 +297,7 @@ lrcc_status build_loop_graph(Ctx* c, const CcArgs& a, cudaGraphExec_t* out) {
 
 lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
                    int32_t* label, const Plan& p) {
-    CcArgs a{src, dst, m, n, label, p.cc_hook == 1 ? 1 : 2, 0};
+    CcArgs a{src, dst, m, n, label, std::min(std::max(p.cc_hook, 1), 3), 0};
     int lg = 0;
     while ((int64_t(1) << lg) < n) ++lg;
     a.cap = p.cc_max_rounds > 0 ? p.cc_max_rounds : 64 + 4 * lg;

@@ -17,11 +17,13 @@ struct DevCtl {
     int flag;            // component loop: some edge joined two roots this pass
     int rounds;          // component loop: hook passes so far
     int jump_rounds;     // pointer-jumping rounds (stats)
-    int spl_count[8];    // ruling set: non-head splitters claimed at each level
     int work[8];         // ruling set: next splitter to walk at each level
     int err_where;       // index that raised the error (debugging aid)
     int batch_next;      // batched kernels: next instance to take
-    int pad[2];
+    int ovf_next;        // read-only walk: overflow chunks claimed
+    int pairs;           // read-only walk: (element, rank) pairs produced
+    int place_next;      // read-only walk: next pair slice to place
+    int pad[7];
 };
 
 __device__ __forceinline__ void record_error(DevCtl* c, int code, int where = -1) {
@@ -72,6 +74,19 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
     return v;
 }
 
+// Load through L1 with an L2 eviction-priority hint (for arrays that should
+// stay resident in L2 while other data streams past).
+__device__ __forceinline__ int32_t ld_hint(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_cg_hint(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Load that bypasses L1 (sees other SMs' atomics sooner than an L1 hit would).
 __device__ __forceinline__ int32_t ld_cg(const int32_t* p) {
     int32_t v;
@@ -86,9 +101,8 @@ __device__ __forceinline__ uint64_t ld_cg_u64(const uint64_t* p) {
 
 // ------------------------------------------------------------------ hash --
 
-// Splitter choice: element i is a splitter when a 32-bit mix of (i, seed)
-// falls below thr = 2^32 / spacing. The mixer is the finaliser of
-// MurmurHash3 (Appleby, public domain). Results never depend on the choice.
+// 32-bit mixer: the finaliser of MurmurHash3 (Appleby, public domain). Used
+// to place splitters; results never depend on where they fall.
 __host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -96,9 +110,6 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     h *= 0xc2b2ae35u;
     h ^= h >> 16;
     return h;
-}
-__device__ __forceinline__ bool pick(uint32_t i, uint32_t seed, uint32_t thr) {
-    return mix32(i * 0x9E3779B1u + seed) < thr;
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

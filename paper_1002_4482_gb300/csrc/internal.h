@@ -13,6 +13,7 @@
 namespace lrcc {
 
 struct DevCtl;
+struct Ctx;
 
 constexpr int KIND_LR = 1;
 constexpr int KIND_LR_WYLLIE = 2;
@@ -25,8 +26,9 @@ struct Plan {
     int rs_spacing0 = 32;
     int rs_spacing = 16;
     int rs_small = 8192;
-    int rs_chains = 2;
-    int cc_hook = 2;
+    int rs_chains = 1;
+    int rs_level0 = 2;      // 1 = in-place walk words, 2 = read-only walk + chunked records
+    int cc_hook = 1;
     int cc_max_rounds = 0;
     int use_graphs = 1;
     uint64_t seed = 0x5eedULL;
@@ -37,20 +39,26 @@ Plan plan_for(int kind, int64_t n);
 constexpr int MAX_LEVELS = 8;
 struct RsLayout {
     int levels = 0;                 // L: levels with a walk; level L is ranked by one block
+                                    // size[l+1] = ceil(size[l] / 2^logD[l]) splitters at level l
     int64_t size[MAX_LEVELS + 1];   // element bound of each level (size[0] = n)
-    uint32_t thr[MAX_LEVELS];       // splitter threshold of each walked level
+    int logD[MAX_LEVELS];           // log2 of the splitter spacing of each walked level
     size_t off_R[MAX_LEVELS + 1], off_snext[MAX_LEVELS + 1], off_sw[MAX_LEVELS + 1],
         off_S[MAX_LEVELS + 1];
     size_t off_W0 = 0;
+    bool readonly = false;          // level 0 by the read-only walk (chunks, scan, scatter, place)
+    int64_t grid = 0, cap = 0, ovf_cap = 0;
+    size_t off_ids = 0, off_meta = 0, off_ovf_owner = 0, off_fill = 0, off_ovf_used = 0, off_counts = 0, off_totals = 0,
+        off_vis = 0;
     size_t bytes = 0;
 };
-RsLayout rs_layout(int64_t n, const Plan& p);
+RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid);
+int rs_walk_grid(Ctx* c, const Plan& p);
 
 // Phase ids for timing mode (names in runtime.cu).
 enum Phase {
     PH_SELECT0, PH_WALK0, PH_SELECT, PH_WALK, PH_FINAL, PH_EXPAND, PH_EXPAND0, PH_SMALL,
     PH_WY_PACK, PH_WY_JUMP, PH_WY_FINAL, PH_CC_INIT, PH_CC_LOOP, PH_CC_HOOK, PH_CC_SHORTCUT,
-    PH_LR_BATCH, PH_CC_BATCH, PH_BATCH_PREP, PH_COUNT
+    PH_LR_BATCH, PH_CC_BATCH, PH_BATCH_PREP, PH_SCAN, PH_SCATTER, PH_COUNT
 };
 
 struct GraphEntry {

@@ -3,9 +3,8 @@
 //
 // Ruling set, as built here for sm_103a:
 //   select   (RS1+RS2) one streaming pass packs succ into 8-byte words
-//            W[i] = (next | splitter flag, splitter index or weight 1) and
-//            compacts the randomly chosen splitters (the head is always
-//            splitter 0);
+//            W[i] = (next | splitter flag, splitter index or weight 1); one
+//            random splitter per block of D indices, the head is splitter 0;
 //   walk     (RS3) every splitter's sublist is walked once; each visited
 //            word is overwritten IN PLACE with (prefix weight, owner | VIS),
 //            so a step costs one random sector read plus its write-back;
@@ -102,12 +101,11 @@ __global__ void __launch_bounds__(FINAL_THREADS, 1)
 // suffix weights S. The head splitter (index 0) must see the whole list.
 template <int PER>
 __global__ void __launch_bounds__(FINAL_THREADS, 1)
-    rs_final_kernel(const uint64_t* __restrict__ R, const int* cnt, int cap, int32_t* __restrict__ S,
-                    int64_t expect, DevCtl* ctl) {
+    rs_final_kernel(const uint64_t* __restrict__ R, int r, int32_t* __restrict__ S, int64_t expect,
+                    DevCtl* ctl) {
     extern __shared__ int sm[];
     int* val = sm;
     int* nxt = sm + PER * FINAL_THREADS;
-    const int r = min(1 + *cnt, cap);
     for (int j = threadIdx.x; j < r; j += FINAL_THREADS) {
         const uint64_t w = R[j];
         nxt[j] = (int)lo32(w);
@@ -122,21 +120,32 @@ __global__ void __launch_bounds__(FINAL_THREADS, 1)
 
 // ------------------------------------------------------------ ruling set
 
-// Level-0 select: pack succ into walk words and compact the splitters.
-// Warps stride over groups of 4 elements (Sec. 2.5 striding), so loads and
-// stores are 16-byte and coalesced.
+// Splitter choice (Sec. 3.2, RS2), stratified: the elements are cut into
+// blocks of D = 2^logD consecutive indices and each block contributes exactly
+// one splitter at a hashed offset, so a splitter's index is its block number
+// and no compaction is needed. The head's block takes the head as its
+// splitter, and block numbers are rotated so that the head is splitter 0.
+// Offsets come from the MurmurHash3 finaliser of (block, seed).
+__device__ __forceinline__ uint32_t block_offset(uint32_t b, uint32_t size, uint32_t seed) {
+    return static_cast<uint32_t>((static_cast<uint64_t>(mix32(b * 0x9E3779B1u + seed)) * size) >> 32);
+}
+
+// Level-0 select: one streaming pass packs succ into walk words
+// W[i] = (next | SPL, splitter index) for splitters, (next, weight 1) for the
+// rest, and records each splitter's successor and weight. Warps stride over
+// groups of 4 elements (Sec. 2.5), with 16-byte loads and stores.
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK)
     rs_select0(const int32_t* __restrict__ succ, int64_t n, int32_t head, uint64_t* __restrict__ W,
-               int32_t* __restrict__ snext, int32_t* __restrict__ sw, int cap, uint32_t thr,
-               uint32_t seed, DevCtl* ctl) {
+               int32_t* __restrict__ snext, int32_t* __restrict__ sw, int logD, int64_t nb, uint32_t seed,
+               DevCtl* ctl) {
     const uint64_t pol = policy_evict_first();
-    const int lane = threadIdx.x & 31;
+    const int64_t D = int64_t(1) << logD;
+    const int64_t bh = head >> logD;
     const int64_t ngroups = (n + 3) >> 2;
-    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * BLOCK) >> 5;
-    for (int64_t gb = warp * 32; gb < ngroups; gb += nwarps * 32) {
-        const int64_t i0 = (gb + lane) * 4;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
+         g += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int64_t i0 = g * 4;
         int s[4];
         if (VEC && i0 + 3 < n) {
             const int4 v = ld_stream_v4(succ + i0, pol);
@@ -145,51 +154,26 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int q = 0; q < 4; ++q) s[q] = (i0 + q < n) ? ld_stream(succ + i0 + q, pol) : -1;
         }
-        uint32_t nx[4];
-        bool sp[4];
-        int cnt = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t i = i0 + q;
-            const bool valid = i < n;
-            const int v = s[q];
-            const bool tail = (v == -1) | (v == i);
-            const bool bad = !tail && (v < 0 || v >= n);
-            if (valid && bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
-            nx[q] = (tail || bad) ? NIL : (uint32_t)v;
-            sp[q] = valid && i != head && pick((uint32_t)i, seed, thr);
-            cnt += sp[q];
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int base = 0;
-        if (lane == 31 && total) base = atomicAdd(&ctl->spl_count[0], total);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int j = 1 + base + incl - cnt;
+        // D >= 4 and i0 % 4 == 0, so the 4 elements share one block
+        const int64_t b = i0 >> logD;
+        const uint32_t size = (uint32_t)min(D, n - (b << logD));
+        const uint32_t off = b == bh ? (uint32_t)(head - (b << logD)) : block_offset((uint32_t)b, size, seed);
+        const int64_t j = b >= bh ? b - bh : b - bh + nb;
         uint64_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t i = i0 + q;
-            if (i == head) {
-                w[q] = pack(nx[q] | SPL, 0);
-                snext[0] = (int32_t)nx[q];
-                sw[0] = 1;
-            } else if (sp[q]) {
-                if (j < cap) {
-                    w[q] = pack(nx[q] | SPL, (uint32_t)j);
-                    snext[j] = (int32_t)nx[q];
-                    sw[j] = 1;
-                } else {
-                    w[q] = pack(nx[q], 1);
-                }
-                ++j;
+            const int v = s[q];
+            const bool tail = (v == -1) | (v == i);
+            const bool bad = !tail && (v < 0 || v >= n);
+            if (i < n && bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+            const uint32_t nx = (tail || bad) ? NIL : (uint32_t)v;
+            if (i < n && (uint32_t)(i - (b << logD)) == off) {
+                w[q] = pack(nx | SPL, (uint32_t)j);
+                snext[j] = (int32_t)nx;
+                sw[j] = 1;
             } else {
-                w[q] = pack(nx[q], 1);
+                w[q] = pack(nx, 1);
             }
         }
         if (i0 + 3 < n) {
@@ -205,34 +189,22 @@ __global__ void __launch_bounds__(BLOCK)
 }
 
 // Select at level >= 1: the elements are the previous level's splitters,
-// whose packed words R[j] = (next, weight) are already walk words. Only the
-// chosen splitters are read and rewritten as (next | SPL, new index).
+// whose packed words R[j] = (next, weight) are already walk words; the head
+// is element 0. One thread per block rewrites its splitter's word as
+// (next | SPL, block) and records its successor and weight.
 __global__ void __launch_bounds__(BLOCK)
-    rs_select(uint64_t* __restrict__ R, const int* cnt_in, int cap_in, int32_t* __restrict__ snext,
-              int32_t* __restrict__ sw, int cap, uint32_t thr, uint32_t seed, int* cnt_out) {
-    const int r = min(1 + *cnt_in, cap_in);
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * BLOCK) >> 5;
-    for (int jb = warp * 32; jb < r; jb += nwarps * 32) {
-        const int j = jb + lane;
-        const bool sp = j < r && j != 0 && pick((uint32_t)j, seed, thr);
-        const unsigned m = __ballot_sync(0xffffffffu, sp);
-        int base = 0;
-        if (lane == 0 && m) base = atomicAdd(cnt_out, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const int jj = 1 + base + __popc(m & lanemask_lt());
-        if (j == 0) {
-            const uint64_t w = R[0];
-            R[0] = pack(lo32(w) | SPL, 0);
-            snext[0] = (int32_t)lo32(w);
-            sw[0] = (int32_t)hi32(w);
-        } else if (sp && jj < cap) {
-            const uint64_t w = R[j];
-            R[j] = pack(lo32(w) | SPL, (uint32_t)jj);
-            snext[jj] = (int32_t)lo32(w);
-            sw[jj] = (int32_t)hi32(w);
-        }
+    rs_select(uint64_t* __restrict__ R, int64_t nl, int32_t* __restrict__ snext, int32_t* __restrict__ sw,
+              int logD, int64_t nb, uint32_t seed) {
+    const int64_t D = int64_t(1) << logD;
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; b < nb;
+         b += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const uint32_t size = (uint32_t)min(D, nl - (b << logD));
+        const uint32_t off = b == 0 ? 0u : block_offset((uint32_t)b, size, seed);
+        const int64_t sidx = (b << logD) + off;
+        const uint64_t w = R[sidx];
+        R[sidx] = pack(lo32(w) | SPL, (uint32_t)b);
+        snext[b] = (int32_t)lo32(w);
+        sw[b] = (int32_t)hi32(w);
     }
 }
 
@@ -243,10 +215,8 @@ __global__ void __launch_bounds__(BLOCK)
 template <int K>
 __global__ void __launch_bounds__(BLOCK)
     rs_walk(uint64_t* __restrict__ W, const int32_t* __restrict__ snext, const int32_t* __restrict__ sw,
-            uint64_t* __restrict__ Rout, const int* cnt, int cap, int* work, int64_t nlevel,
-            DevCtl* ctl) {
+            uint64_t* __restrict__ Rout, int r, int* work, int64_t nlevel, DevCtl* ctl) {
     constexpr int CHUNK = 64;
-    const int r = min(1 + *cnt, cap);
     const int lane = threadIdx.x & 31;
     int pool = 0, pool_end = 0;
     bool exhausted = false;
@@ -324,11 +294,421 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+// ------------------------------------------------ level 0, read-only walk
+//
+// Random HBM accesses are limited by row activations, not bytes: a random
+// read costs one activation, a random read-modify-write two. This level-0
+// path therefore walks succ READ-ONLY (one activation per element) and never
+// writes a per-element word at a random place:
+//   walk     each walk buffers the elements it visits in registers and
+//            writes them 8 at a time as one 32-byte chunk (ids in visiting
+//            order, plus (first position k0, owner j)) into its block's
+//            region; the block also counts its elements per coarse id
+//            bucket (NBK buckets of consecutive ids);
+//   scan     the per-(bucket, block) counts become output offsets;
+//   scatter  each block turns its chunks into (element, rank) pairs with one
+//            gather of the owner's suffix weight per chunk, written grouped
+//            by bucket;
+//   place    the pairs, in bucket order, write rank[element]; the writes of
+//            one bucket fall in a window of a few MB that stays in L2, so
+//            lines are complete before they are written back.
+// A walk that runs longer than `careful` steps marks the elements it visits
+// in a bitmap and stops with an error on a repeat, so a cycle without a
+// splitter cannot trap it; valid lists never repeat an element.
+
+constexpr int CIDS = 8;        // element ids per chunk (one 32-byte sector)
+constexpr int NBK_LOG = 8;
+constexpr int NBK = 1 << NBK_LOG;
+
+struct Level0 {
+    int64_t n, nb, bh;   // elements, splitters (blocks), the head's block
+    int logD;
+    uint32_t head_off;   // offset of the head inside its block
+    uint32_t seed;
+};
+
+struct Chunks {
+    int32_t* ids;        // chunk c: ids[8c .. 8c+8), unused slots -1
+    uint64_t* meta;      // meta[c] = k0 << 32 | j
+    int32_t* ovf_owner;  // block that wrote overflow chunk o
+    int* fill;           // chunks written into each block's own region
+    int* ovf_used;       // overflow chunks each block took
+    int* counts;         // [NBK][grid] elements per (bucket, block); then row offsets
+    int* totals;         // [NBK] elements per bucket
+    uint32_t* vis;       // careful-mode marks, one bit per element
+    int64_t cap;         // chunks per block region
+    int64_t ovf_cap;     // overflow chunks
+    int64_t ovf_base;    // index of the first overflow chunk (= grid * cap)
+    int shift;           // coarse bucket of element x = x >> shift
+    int64_t careful;     // steps after which a walk marks what it visits
+};
+
+// Index of x among the level-0 splitters, or -1 if x is not one.
+__device__ __forceinline__ int64_t splitter_index0(int64_t x, const Level0& L0) {
+    const int64_t D = int64_t(1) << L0.logD;
+    const int64_t b = x >> L0.logD;
+    const uint32_t size = (uint32_t)min(D, L0.n - (b << L0.logD));
+    const uint32_t off = b == L0.bh ? L0.head_off : block_offset((uint32_t)b, size, L0.seed);
+    if ((uint32_t)(x - (b << L0.logD)) != off) return -1;
+    return b >= L0.bh ? b - L0.bh : b - L0.bh + L0.nb;
+}
+
+// Element of splitter j.
+__device__ __forceinline__ int64_t splitter_node0(int64_t j, const Level0& L0) {
+    const int64_t D = int64_t(1) << L0.logD;
+    int64_t b = j + L0.bh;
+    if (b >= L0.nb) b -= L0.nb;
+    const uint32_t size = (uint32_t)min(D, L0.n - (b << L0.logD));
+    const uint32_t off = b == L0.bh ? L0.head_off : block_offset((uint32_t)b, size, L0.seed);
+    return (b << L0.logD) + off;
+}
+
+// Read-only sublist walk (RS3). Warps claim splitters in chunks of 64 and
+// hand them to lanes as their walks end (the hardware scheduler then
+// balances the uneven sublists, Sec. 3.2).
+template <int K>
+__global__ void __launch_bounds__(BLOCK)
+    rs_walk0c(const int32_t* __restrict__ succ, Level0 L0, Chunks C, uint64_t* __restrict__ R1, int* work,
+              DevCtl* ctl) {
+    constexpr int WCHUNK = 64;
+    __shared__ int s_fill, s_ovf;
+    __shared__ int s_cnt[NBK];
+    for (int t = threadIdx.x; t < NBK; t += BLOCK) s_cnt[t] = 0;
+    if (threadIdx.x == 0) s_fill = s_ovf = 0;
+    __syncthreads();
+    const int64_t r = L0.nb;
+    const int lane = threadIdx.x & 31;
+    int pool = 0, pool_end = 0;
+    bool exhausted = false;
+    int64_t j[K], cur[K];
+    uint32_t k[K], k0[K];
+    int bn[K];
+    int32_t buf[K][CIDS];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        j[q] = -1;
+        cur[q] = 0;
+        k[q] = k0[q] = 0;
+        bn[q] = 0;
+    }
+    for (;;) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            bool need = j[q] < 0;
+            unsigned m = __ballot_sync(0xffffffffu, need);
+            while (m && !exhausted) {
+                if (pool >= pool_end) {
+                    int b = 0;
+                    if (lane == 0) b = atomicAdd(work, WCHUNK);
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    if (b >= r) {
+                        exhausted = true;
+                        break;
+                    }
+                    pool = b;
+                    pool_end = (int)min((int64_t)b + WCHUNK, r);
+                }
+                const int avail = pool_end - pool;
+                const int rk = __popc(m & lanemask_lt());
+                if (need && rk < avail) {
+                    j[q] = pool + rk;
+                    cur[q] = splitter_node0(j[q], L0);
+                    k[q] = k0[q] = 0;
+                    bn[q] = 0;
+                    need = false;
+                }
+                pool += min(avail, __popc(m));
+                m = __ballot_sync(0xffffffffu, need);
+            }
+        }
+        bool act = false;
+#pragma unroll
+        for (int q = 0; q < K; ++q) act |= j[q] >= 0;
+        if (!__any_sync(0xffffffffu, act)) break;
+        int32_t nx[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) nx[q] = j[q] >= 0 ? __ldcs(succ + cur[q]) : -1;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (j[q] < 0) continue;
+            bool end = false, bad = false;
+            if (k[q] >= C.careful) {
+                const uint32_t bit = 1u << (cur[q] & 31);
+                if (atomicOr(C.vis + (cur[q] >> 5), bit) & bit) bad = true;   // element reached twice
+            }
+#pragma unroll
+            for (int t = 0; t < CIDS; ++t)
+                if (bn[q] == t) buf[q][t] = (int32_t)cur[q];
+            ++bn[q];
+            const int64_t x = nx[q];
+            uint64_t rw = 0;
+            if (bad) {
+                end = true;
+            } else if (x == -1 || x == cur[q]) {
+                rw = pack(NIL, k[q] + 1);
+                end = true;
+            } else if (x < 0 || x >= L0.n) {
+                bad = end = true;
+            } else {
+                const int64_t sj = splitter_index0(x, L0);
+                if (sj >= 0) {
+                    rw = pack((uint32_t)sj, k[q] + 1);
+                    end = true;
+                }
+            }
+            if (bad) {
+                record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)cur[q]);
+                rw = pack(NIL, k[q] + 1);
+            }
+            if (bn[q] == CIDS || end) {
+                // flush one chunk: own region first, then the shared overflow pool
+                const int slot = atomicAdd(&s_fill, 1);
+                int64_t c = -1;
+                if (slot < C.cap) {
+                    c = (int64_t)blockIdx.x * C.cap + slot;
+                } else {
+                    const int o = atomicAdd(&ctl->ovf_next, 1);
+                    if (o < C.ovf_cap) {
+                        c = C.ovf_base + o;
+                        C.ovf_owner[o] = blockIdx.x;
+                        atomicAdd(&s_ovf, 1);
+                    } else {
+                        record_error(ctl, LRCC_ERR_INVALID_INPUT, -4);
+                    }
+                }
+                if (c >= 0) {
+                    int32_t v[CIDS];
+#pragma unroll
+                    for (int t = 0; t < CIDS; ++t) v[t] = t < bn[q] ? buf[q][t] : -1;
+                    int4* d = reinterpret_cast<int4*>(C.ids + c * CIDS);
+                    d[0] = make_int4(v[0], v[1], v[2], v[3]);
+                    d[1] = make_int4(v[4], v[5], v[6], v[7]);
+                    C.meta[c] = (static_cast<uint64_t>(k0[q]) << 32) | static_cast<uint64_t>(j[q]);
+#pragma unroll
+                    for (int t = 0; t < CIDS; ++t)
+                        if (t < bn[q]) atomicAdd(&s_cnt[v[t] >> C.shift], 1);
+                }
+                k0[q] = k[q] + 1;
+                bn[q] = 0;
+            }
+            if (end) {
+                R1[j[q]] = rw;
+                j[q] = -1;
+            } else {
+                cur[q] = x;
+                ++k[q];
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        C.fill[blockIdx.x] = min(s_fill, (int)C.cap);
+        C.ovf_used[blockIdx.x] = s_ovf;
+    }
+    for (int t = threadIdx.x; t < NBK; t += BLOCK) C.counts[(int64_t)t * gridDim.x + blockIdx.x] = s_cnt[t];
+}
+
+// Exclusive scan of each bucket's row of per-block counts, in place, one
+// block per bucket; the row total goes to totals[bucket]. The start of each
+// bucket (a scan over NBK totals) is formed by the scatter blocks themselves.
+constexpr int SCAN_THREADS = 256;
+__global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int G, int* totals) {
+    __shared__ int s_warp[SCAN_THREADS / 32];
+    int* row = counts + (int64_t)blockIdx.x * G;
+    const int per = (G + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int b = threadIdx.x * per, e = min(G, b + per);
+    int sum = 0;
+    for (int i = b; i < e; ++i) sum += row[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < SCAN_THREADS / 32 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < SCAN_THREADS / 32) s_warp[lane] = v;
+    }
+    __syncthreads();
+    int run = (wid ? s_warp[wid - 1] : 0) + incl - sum;
+    for (int i = b; i < e; ++i) {
+        const int c = row[i];
+        row[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) totals[blockIdx.x] = run;
+}
+
+// Chunks of block c -> (element, rank) pairs at the block's offsets of each
+// bucket. Run with the walk's grid, block c taking the walk block c's chunks.
+// Radix-partition style: each round a block loads SCAT_U chunks per thread,
+// ranks the round's pairs by bucket in shared memory, lays them out sorted
+// by bucket in a shared tile and writes every bucket's run with coalesced
+// stores at the block's next offset for that bucket.
+constexpr int SCAT_U = 2;
+constexpr int SCAT_ITEMS = SCAT_U * BLOCK * CIDS;
+__global__ void __launch_bounds__(BLOCK)
+    rs_scatter(Chunks C, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n, DevCtl* ctl) {
+    __shared__ int s_base[NBK];     // next free pair of each bucket for this block
+    __shared__ int s_hist[NBK];     // pairs of each bucket in the current round
+    __shared__ int s_tstart[NBK];   // start of each bucket's run in the tile
+    __shared__ int s_warp[BLOCK / 32];
+    __shared__ int s_items;
+    __shared__ uint64_t s_tile[SCAT_ITEMS];
+    static_assert(NBK == BLOCK, "one thread per bucket");
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    // block-wide exclusive scan of one value per thread (uses s_warp; two syncs)
+    auto block_scan = [&](int v, int* total) {
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        int off = 0, all = 0;
+#pragma unroll
+        for (int w = 0; w < BLOCK / 32; ++w) {
+            const int x = s_warp[w];
+            off += w < wid ? x : 0;
+            all += x;
+        }
+        __syncthreads();
+        *total = all;
+        return off + incl - v;
+    };
+    {
+        int all = 0;
+        const int start = block_scan(C.totals[t], &all);
+        if (t == 0) ctl->pairs = all;
+        s_base[t] = start + C.counts[(int64_t)t * gridDim.x + blockIdx.x];
+        s_hist[t] = 0;
+    }
+    __syncthreads();
+    const int nf = C.fill[blockIdx.x];
+    const bool has_ovf = C.ovf_used[blockIdx.x] > 0;
+    const int64_t no = has_ovf ? min((int64_t)ctl->ovf_next, C.ovf_cap) : 0;
+    const int64_t own0 = (int64_t)blockIdx.x * C.cap;
+    const int64_t nrounds_own = (nf + SCAT_U * BLOCK - 1) / (SCAT_U * BLOCK);
+    const int64_t nrounds = nrounds_own + (no + SCAT_U * BLOCK - 1) / (SCAT_U * BLOCK);
+    for (int64_t rd = 0; rd < nrounds; ++rd) {
+        int64_t ch[SCAT_U];
+#pragma unroll
+        for (int u = 0; u < SCAT_U; ++u) {
+            if (rd < nrounds_own) {
+                const int64_t i = rd * SCAT_U * BLOCK + u * BLOCK + t;
+                ch[u] = i < nf ? own0 + i : -1;
+            } else {
+                const int64_t o = (rd - nrounds_own) * SCAT_U * BLOCK + u * BLOCK + t;
+                ch[u] = (o < no && C.ovf_owner[o] == (int)blockIdx.x) ? C.ovf_base + o : -1;
+            }
+        }
+        int32_t id[SCAT_U][CIDS];
+        int32_t top[SCAT_U];
+#pragma unroll
+        for (int u = 0; u < SCAT_U; ++u) {
+            if (ch[u] >= 0) {
+                const int4* src = reinterpret_cast<const int4*>(C.ids + ch[u] * CIDS);
+                const int4 a = __ldcs(src), b = __ldcs(src + 1);
+                id[u][0] = a.x; id[u][1] = a.y; id[u][2] = a.z; id[u][3] = a.w;
+                id[u][4] = b.x; id[u][5] = b.y; id[u][6] = b.z; id[u][7] = b.w;
+                const uint64_t mt = __ldcs(reinterpret_cast<const unsigned long long*>(C.meta + ch[u]));
+                top[u] = S1[lo32(mt)] - 1 - (int32_t)hi32(mt);
+            } else {
+#pragma unroll
+                for (int q = 0; q < CIDS; ++q) id[u][q] = -1;
+                top[u] = 0;
+            }
+        }
+        int local[SCAT_U][CIDS];
+#pragma unroll
+        for (int u = 0; u < SCAT_U; ++u)
+#pragma unroll
+            for (int q = 0; q < CIDS; ++q)
+                local[u][q] = id[u][q] >= 0 ? atomicAdd(&s_hist[id[u][q] >> C.shift], 1) : 0;
+        __syncthreads();
+        const int h = s_hist[t];
+        int items = 0;
+        const int ts = block_scan(h, &items);
+        s_tstart[t] = ts;
+        s_hist[t] = s_base[t];      // global start of this round's run of bucket t
+        s_base[t] += h;
+        if (t == 0) s_items = items;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < SCAT_U; ++u)
+#pragma unroll
+            for (int q = 0; q < CIDS; ++q)
+                if (id[u][q] >= 0)
+                    s_tile[s_tstart[id[u][q] >> C.shift] + local[u][q]] =
+                        pack((uint32_t)id[u][q], (uint32_t)(top[u] - q));
+        __syncthreads();
+        const int ni = s_items;
+        for (int i = t; i < ni; i += BLOCK) {
+            const uint64_t pr = s_tile[i];
+            const int bk = (int)(lo32(pr) >> C.shift);
+            const int64_t pos = (int64_t)s_hist[bk] + (i - s_tstart[bk]);
+            if (pos < n) pairs[pos] = pr;
+        }
+        __syncthreads();
+        s_hist[t] = 0;
+        __syncthreads();
+    }
+}
+
+// rank[element] from the pairs. Blocks take slices of PLACE_SLICE pairs from
+// one counter in order, so at any moment the pairs in flight cover a few
+// buckets and their rank writes stay in a window that L2 holds until every
+// line is complete (a grid-stride loop would let blocks drift apart and
+// spread the writes over far more memory than L2 holds).
+constexpr int PLACE_SLICE = BLOCK * 64;
+__global__ void __launch_bounds__(BLOCK)
+    rs_place(const uint64_t* __restrict__ pairs, int64_t n, int32_t* __restrict__ rank, DevCtl* ctl) {
+    __shared__ int s_start;
+    const int64_t m = min((int64_t)ctl->pairs, n);
+    for (;;) {
+        if (threadIdx.x == 0) s_start = atomicAdd(&ctl->place_next, PLACE_SLICE);
+        __syncthreads();
+        const int64_t start = s_start;
+        __syncthreads();
+        if (start >= m) break;
+        const int64_t end = min(start + PLACE_SLICE, m);
+        if (end - start == PLACE_SLICE) {
+            // full slice: 16 pairs per thread in flight
+            constexpr int U = PLACE_SLICE / (2 * BLOCK) / 4;
+            for (int w = 0; w < 4; ++w) {
+                ulonglong2 p[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    p[u] = __ldcs(reinterpret_cast<const ulonglong2*>(pairs + start) + (w * U + u) * BLOCK + threadIdx.x);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    rank[lo32(p[u].x)] = (int32_t)hi32(p[u].x);
+                    rank[lo32(p[u].y)] = (int32_t)hi32(p[u].y);
+                }
+            }
+        } else {
+            for (int64_t i = start + threadIdx.x; i < end; i += BLOCK) {
+                const uint64_t p = pairs[i];
+                rank[lo32(p)] = (int32_t)hi32(p);
+            }
+        }
+    }
+}
+
 // Expand at level >= 1: S[c] = S_next[owner] - prefix (RS5).
 __global__ void __launch_bounds__(BLOCK)
-    rs_expand(const uint64_t* __restrict__ W, const int* cnt, int cap, const int32_t* __restrict__ Snext,
+    rs_expand(const uint64_t* __restrict__ W, int r, const int32_t* __restrict__ Snext,
               int32_t* __restrict__ S, DevCtl* ctl) {
-    const int r = min(1 + *cnt, cap);
     for (int c = blockIdx.x * BLOCK + threadIdx.x; c < r; c += gridDim.x * BLOCK) {
         const uint64_t w = W[c];
         const uint32_t lo = lo32(w), hi = hi32(w);
@@ -515,7 +895,13 @@ int stream_grid(Ctx* c, int64_t groups, const void* kernel) {
 
 // --------------------------------------------------------------- planning
 
-RsLayout rs_layout(int64_t n, const Plan& p) {
+int rs_walk_grid(Ctx* c, const Plan& p) {
+    const void* k = p.rs_chains >= 4 ? (const void*)rs_walk0c<4>
+                  : p.rs_chains == 2 ? (const void*)rs_walk0c<2> : (const void*)rs_walk0c<1>;
+    return persistent_grid(c, k, BLOCK);
+}
+
+RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid) {
     RsLayout L;
     L.size[0] = n;
     size_t off = 0;
@@ -524,26 +910,49 @@ RsLayout rs_layout(int64_t n, const Plan& p) {
         off = align_up(off + bytes, 256);
         return o;
     };
+    // in-place walk words, or the (element, rank) pairs of the read-only walk
     L.off_W0 = take(sizeof(uint64_t) * (size_t)n);
     int64_t cur = n;
     int lvl = 0;
     while (cur > p.rs_small && lvl < MAX_LEVELS) {
+        // spacing: a power of two, at least 4 (one block holds whole 4-element groups)
         int64_t spacing = lvl == 0 ? p.rs_spacing0 : p.rs_spacing;
-        spacing = std::max<int64_t>(2, spacing);
-        const double expect = std::ceil((double)cur / (double)spacing);
-        int64_t cap = (int64_t)(expect + 4.0 * std::sqrt(expect) + 32.0);
-        cap = std::min<int64_t>(cap, cur);
-        if (lvl == MAX_LEVELS - 1) cap = std::min<int64_t>(cap, p.rs_small);
-        L.thr[lvl] = (uint32_t)std::min<double>(4294967295.0, 4294967296.0 / (double)spacing);
+        int logD = 2;
+        while (logD < 20 && (int64_t(1) << (logD + 1)) <= spacing) ++logD;
+        if (lvl == MAX_LEVELS - 1)  // last allowed level must fit one block
+            while (logD < 30 && ((cur + (int64_t(1) << logD) - 1) >> logD) > p.rs_small) ++logD;
+        const int64_t nb = (cur + (int64_t(1) << logD) - 1) >> logD;
+        L.logD[lvl] = logD;
         ++lvl;
-        L.size[lvl] = cap;
-        L.off_R[lvl] = take(sizeof(uint64_t) * (size_t)cap);
-        L.off_snext[lvl] = take(sizeof(int32_t) * (size_t)cap);
-        L.off_sw[lvl] = take(sizeof(int32_t) * (size_t)cap);
-        L.off_S[lvl] = take(sizeof(int32_t) * (size_t)cap);
-        cur = cap;
+        L.size[lvl] = nb;
+        L.off_R[lvl] = take(sizeof(uint64_t) * (size_t)nb);
+        L.off_snext[lvl] = take(sizeof(int32_t) * (size_t)nb);
+        L.off_sw[lvl] = take(sizeof(int32_t) * (size_t)nb);
+        L.off_S[lvl] = take(sizeof(int32_t) * (size_t)nb);
+        cur = nb;
     }
     L.levels = lvl;
+    L.readonly = p.rs_level0 == 2 && lvl > 0 && walk_grid > 0;
+    if (L.readonly) {
+        const int64_t G = walk_grid;
+        L.grid = G;
+        // own region per block: its share of the elements in chunks of 8, plus
+        // the padding of its share of the sublists, with 30 % slack
+        L.cap = (int64_t)(1.1 * (double)n / (double)G / CIDS + 0.6 * (double)L.size[1] / (double)G) + 16;
+        // the shared pool alone can hold every chunk of a valid list (at most
+        // n/8 full chunks plus one partial chunk per sublist), however unevenly
+        // the sublists fall on the blocks
+        L.ovf_cap = n / CIDS + L.size[1] + 1024;
+        const int64_t chunks = G * L.cap + L.ovf_cap;
+        L.off_ids = take(sizeof(int32_t) * CIDS * (size_t)chunks);
+        L.off_meta = take(sizeof(uint64_t) * (size_t)chunks);
+        L.off_ovf_owner = take(sizeof(int32_t) * (size_t)L.ovf_cap);
+        L.off_fill = take(sizeof(int) * (size_t)G);
+        L.off_ovf_used = take(sizeof(int) * (size_t)G);
+        L.off_counts = take(sizeof(int) * (size_t)NBK * (size_t)G);
+        L.off_totals = take(sizeof(int) * (size_t)NBK);
+        L.off_vis = take(sizeof(uint32_t) * (size_t)((n + 31) / 32));
+    }
     L.bytes = off;
     return L;
 }
@@ -567,71 +976,110 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     // level 0
     const bool vec = aligned16(succ);
     const int64_t groups = (n + 3) / 4;
-    {
+    if (!L.readonly) {
         const void* k = vec ? (const void*)rs_select0<true> : (const void*)rs_select0<false>;
         const int g = stream_grid(c, groups, k);
         phase_begin(c, s);
         if (vec)
-            rs_select0<true><<<g, BLOCK, 0, s>>>(succ, n, head, W0, SN(1), SW(1), (int)L.size[1], L.thr[0],
-                                                 seed0, ctl);
+            rs_select0<true><<<g, BLOCK, 0, s>>>(succ, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1], seed0, ctl);
         else
-            rs_select0<false><<<g, BLOCK, 0, s>>>(succ, n, head, W0, SN(1), SW(1), (int)L.size[1], L.thr[0],
-                                                  seed0, ctl);
+            rs_select0<false><<<g, BLOCK, 0, s>>>(succ, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1], seed0, ctl);
         phase_end(c, s, PH_SELECT0);
     }
+    Level0 L0;
+    L0.n = n;
+    L0.nb = L.size[1];
+    L0.logD = L.logD[0];
+    L0.bh = (int64_t)head >> L0.logD;
+    L0.head_off = (uint32_t)(head - (L0.bh << L0.logD));
+    L0.seed = seed0;
+    Chunks C;
+    C.ids = reinterpret_cast<int32_t*>(base + L.off_ids);
+    C.meta = reinterpret_cast<uint64_t*>(base + L.off_meta);
+    C.ovf_owner = reinterpret_cast<int32_t*>(base + L.off_ovf_owner);
+    C.fill = reinterpret_cast<int*>(base + L.off_fill);
+    C.ovf_used = reinterpret_cast<int*>(base + L.off_ovf_used);
+    C.counts = reinterpret_cast<int*>(base + L.off_counts);
+    C.totals = reinterpret_cast<int*>(base + L.off_totals);
+    C.vis = reinterpret_cast<uint32_t*>(base + L.off_vis);
+    C.cap = L.cap;
+    C.ovf_cap = L.ovf_cap;
+    C.ovf_base = L.grid * L.cap;
+    int lg = 0;
+    while ((int64_t(1) << lg) < n) ++lg;
+    C.shift = std::max(0, lg - NBK_LOG);
+    C.careful = int64_t(32) << L.logD[0];
     auto walk = [&](int l, uint64_t* Wl, int64_t nl) {
-        const int* cnt = &ctl->spl_count[l];
-        const int cap = (int)L.size[l + 1];
+        const int r = (int)L.size[l + 1];
         int* work = &ctl->work[l];
         phase_begin(c, s);
         if (p.rs_chains >= 4) {
             const int g = persistent_grid(c, (const void*)rs_walk<4>, BLOCK);
-            rs_walk<4><<<g, BLOCK, 0, s>>>(Wl, SN(l + 1), SW(l + 1), R(l + 1), cnt, cap, work, nl, ctl);
+            rs_walk<4><<<g, BLOCK, 0, s>>>(Wl, SN(l + 1), SW(l + 1), R(l + 1), r, work, nl, ctl);
         } else if (p.rs_chains == 2) {
             const int g = persistent_grid(c, (const void*)rs_walk<2>, BLOCK);
-            rs_walk<2><<<g, BLOCK, 0, s>>>(Wl, SN(l + 1), SW(l + 1), R(l + 1), cnt, cap, work, nl, ctl);
+            rs_walk<2><<<g, BLOCK, 0, s>>>(Wl, SN(l + 1), SW(l + 1), R(l + 1), r, work, nl, ctl);
         } else {
             const int g = persistent_grid(c, (const void*)rs_walk<1>, BLOCK);
-            rs_walk<1><<<g, BLOCK, 0, s>>>(Wl, SN(l + 1), SW(l + 1), R(l + 1), cnt, cap, work, nl, ctl);
+            rs_walk<1><<<g, BLOCK, 0, s>>>(Wl, SN(l + 1), SW(l + 1), R(l + 1), r, work, nl, ctl);
         }
         phase_end(c, s, l == 0 ? PH_WALK0 : PH_WALK);
     };
-    walk(0, W0, n);
+    if (L.readonly) {
+        cudaMemsetAsync(C.vis, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
+        const int G = (int)L.grid;
+        phase_begin(c, s);
+        if (p.rs_chains >= 4) rs_walk0c<4><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
+        else if (p.rs_chains == 2) rs_walk0c<2><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
+        else rs_walk0c<1><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
+        phase_end(c, s, PH_WALK0);
+        phase_begin(c, s);
+        rs_scan_counts<<<NBK, SCAN_THREADS, 0, s>>>(C.counts, G, C.totals);
+        phase_end(c, s, PH_SCAN);
+    } else {
+        walk(0, W0, n);
+    }
     for (int l = 1; l < L.levels; ++l) {
         const uint32_t seed = mix32(seed0 + 0x9E3779B9u * (uint32_t)l);
-        const int g = stream_grid(c, (L.size[l] + 3) / 4, (const void*)rs_select);
+        const int g = stream_grid(c, L.size[l + 1], (const void*)rs_select);
         phase_begin(c, s);
-        rs_select<<<g, BLOCK, 0, s>>>(R(l), &ctl->spl_count[l - 1], (int)L.size[l], SN(l + 1), SW(l + 1),
-                                      (int)L.size[l + 1], L.thr[l], seed, &ctl->spl_count[l]);
+        rs_select<<<g, BLOCK, 0, s>>>(R(l), L.size[l], SN(l + 1), SW(l + 1), L.logD[l], L.size[l + 1], seed);
         phase_end(c, s, PH_SELECT);
         walk(l, R(l), L.size[l]);
     }
     {
         const int lf = L.levels;
-        const int per = small_per((int)L.size[lf]);
+        const int r = (int)L.size[lf];
+        const int per = small_per(r);
         const size_t smem = 2 * sizeof(int) * per * FINAL_THREADS;
-        const int* cnt = &ctl->spl_count[lf - 1];
-        const int cap = (int)L.size[lf];
         phase_begin(c, s);
         if (per == 4) {
             cudaFuncSetAttribute((const void*)rs_final_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            rs_final_kernel<4><<<1, FINAL_THREADS, smem, s>>>(R(lf), cnt, cap, S(lf), n, ctl);
+            rs_final_kernel<4><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), n, ctl);
         } else if (per == 8) {
             cudaFuncSetAttribute((const void*)rs_final_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            rs_final_kernel<8><<<1, FINAL_THREADS, smem, s>>>(R(lf), cnt, cap, S(lf), n, ctl);
+            rs_final_kernel<8><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), n, ctl);
         } else {
             cudaFuncSetAttribute((const void*)rs_final_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            rs_final_kernel<16><<<1, FINAL_THREADS, smem, s>>>(R(lf), cnt, cap, S(lf), n, ctl);
+            rs_final_kernel<16><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), n, ctl);
         }
         phase_end(c, s, PH_FINAL);
     }
     for (int l = L.levels - 1; l >= 1; --l) {
         const int g = stream_grid(c, L.size[l], (const void*)rs_expand);
         phase_begin(c, s);
-        rs_expand<<<g, BLOCK, 0, s>>>(R(l), &ctl->spl_count[l - 1], (int)L.size[l], S(l + 1), S(l), ctl);
+        rs_expand<<<g, BLOCK, 0, s>>>(R(l), (int)L.size[l], S(l + 1), S(l), ctl);
         phase_end(c, s, PH_EXPAND);
     }
-    {
+    if (L.readonly) {
+        phase_begin(c, s);
+        rs_scatter<<<(int)L.grid, BLOCK, 0, s>>>(C, S(1), W0, n, ctl);
+        phase_end(c, s, PH_SCATTER);
+        const int g = 2 * c->sms;
+        phase_begin(c, s);
+        rs_place<<<g, BLOCK, 0, s>>>(W0, n, rank, ctl);
+        phase_end(c, s, PH_EXPAND0);
+    } else {
         const bool v = vec && aligned16(rank);
         const void* k = v ? (const void*)rs_expand0<true> : (const void*)rs_expand0<false>;
         const int g = stream_grid(c, groups, k);

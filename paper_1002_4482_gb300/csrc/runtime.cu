@@ -21,7 +21,7 @@ std::atomic<int> g_timing{0};
 const char* const kPhaseNames[PH_COUNT] = {
     "rs_select0", "rs_walk0", "rs_select", "rs_walk", "rs_final", "rs_expand", "rs_expand0", "lr_small",
     "wy_pack", "wy_jump", "wy_final", "cc_init", "cc_loop", "cc_hook", "cc_shortcut",
-    "lr_batch", "cc_batch", "batch_prep"};
+    "lr_batch", "cc_batch", "batch_prep", "rs_scan", "rs_scatter"};
 std::map<std::pair<int, cudaStream_t>, Ctx*> g_ctx;
 std::mutex g_plan_mu;
 bool g_plan_init = false;
@@ -36,7 +36,11 @@ int log2_ceil(int64_t n) {
 void init_plans_locked() {
     if (g_plan_init) return;
     for (int k = 0; k < 6; ++k)
-        for (int l = 0; l <= 32; ++l) g_plan[k][l] = Plan{};
+        for (int l = 0; l <= 32; ++l) {
+            g_plan[k][l] = Plan{};
+            // the read-only first level pays off once the list is well beyond L2
+            if (l < 25) g_plan[k][l].rs_level0 = 1;
+        }
     g_plan_init = true;
 }
 
@@ -90,7 +94,7 @@ lrcc_status launch_recorded(Ctx* c, const Plan& p, std::vector<uint64_t> key,
 
 std::vector<uint64_t> plan_key(const Plan& p) {
     return {(uint64_t)p.rs_spacing0, (uint64_t)p.rs_spacing, (uint64_t)p.rs_small, (uint64_t)p.rs_chains,
-            (uint64_t)p.cc_hook, (uint64_t)p.cc_max_rounds, p.seed};
+            (uint64_t)p.rs_level0, (uint64_t)p.cc_hook, (uint64_t)p.cc_max_rounds, p.seed};
 }
 
 }  // namespace
@@ -246,7 +250,7 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     const Plan p = plan_for(KIND_LR, n);
-    const RsLayout L = rs_layout(n, p);
+    const RsLayout L = rs_layout(n, p, rs_walk_grid(c, p));
     if (n > p.rs_small) {
         st = ensure_ws(c, L.bytes);
         if (st != LRCC_OK) return st;
@@ -360,8 +364,7 @@ lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out) {
     std::memset(out, 0, sizeof(*out));
     out->kind = c->last_kind;
     out->levels = c->last_levels;
-    for (int l = 0; l < c->last_levels && l < 8; ++l)
-        out->splitters[l] = std::min<int64_t>(1 + (int64_t)h.spl_count[l], c->last_splitter_cap[l]);
+    for (int l = 0; l < c->last_levels && l < 8; ++l) out->splitters[l] = c->last_splitter_cap[l];
     out->rounds = h.rounds;
     out->jump_rounds = h.jump_rounds;
     return LRCC_OK;
@@ -372,8 +375,8 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
     if (plan->rs_small < 0 || plan->rs_small > 16384 || plan->rs_spacing0 < 0 || plan->rs_spacing < 0 ||
         (plan->rs_spacing0 > 0 && plan->rs_spacing0 < 2) || (plan->rs_spacing > 0 && plan->rs_spacing < 2) ||
         (plan->rs_small > 0 && plan->rs_small < 1024) || plan->rs_chains < 0 || plan->rs_chains > 4 ||
-        plan->cc_hook < 0 || plan->cc_hook > 2 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
-        plan->use_graphs > 2)
+        plan->cc_hook < 0 || plan->cc_hook > 3 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
+        plan->use_graphs > 2 || plan->rs_level0 < 0 || plan->rs_level0 > 2)
         return LRCC_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_plan_mu);
     init_plans_locked();
@@ -386,6 +389,7 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
         if (plan->cc_hook) p.cc_hook = plan->cc_hook;
         if (plan->cc_max_rounds) p.cc_max_rounds = plan->cc_max_rounds < 0 ? 0 : plan->cc_max_rounds;
         if (plan->use_graphs) p.use_graphs = plan->use_graphs;
+        if (plan->rs_level0) p.rs_level0 = plan->rs_level0;
         if (plan->seed) p.seed = plan->seed;
     }
     return LRCC_OK;
@@ -402,8 +406,24 @@ lrcc_status lrcc_get_plan(int kind, int64_t n, lrcc_plan* out) {
     out->cc_hook = p.cc_hook;
     out->cc_max_rounds = p.cc_max_rounds;
     out->use_graphs = p.use_graphs;
+    out->rs_level0 = p.rs_level0;
     out->seed = p.seed;
     return LRCC_OK;
+}
+
+lrcc_status lrcc_set_l2_fetch_granularity(int bytes) {
+    if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128) return LRCC_ERR_ARG;
+    if (bytes == 0) return LRCC_OK;
+    return cuda_status(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes));
+}
+
+int lrcc_get_l2_fetch_granularity(void) {
+    size_t v = 0;
+    if (cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int)v;
 }
 
 lrcc_status lrcc_set_timing(int enable) {
@@ -471,7 +491,10 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
     if (n < 0) return -1;
     const Plan p = plan_for(kind, n);
     switch (kind) {
-        case KIND_LR: return n > p.rs_small ? (int64_t)rs_layout(n, p).bytes : 0;
+        case KIND_LR: {
+            // block count of the walk as on a GB300 (152 SMs x 8 blocks) when no device is queried
+            return n > p.rs_small ? (int64_t)rs_layout(n, p, 152 * 8).bytes : 0;
+        }
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
         case KIND_CC: return 0;
         case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n);

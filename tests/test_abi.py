@@ -76,12 +76,19 @@ def test_plan_table_roundtrip(lib):
     with pytest.raises(lrcc.LrccError):
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_small=100000)
     with pytest.raises(lrcc.LrccError):
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=3)
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=4)
 
 
 def test_workspace_query(lib):
     L = lrcc.load()
     assert L.lrcc_workspace_query(lrcc.KIND_LR, 1000, 0) == 0          # one block, no workspace
     big = L.lrcc_workspace_query(lrcc.KIND_LR, 1 << 28, 0)
-    assert 8 * (1 << 28) <= big < 10 * (1 << 28)                        # 8-byte walk words + small levels
+    # read-only first level: 8-byte pairs + ~8 bytes of chunked records + small deeper levels
+    assert 18 * (1 << 28) <= big < 23 * (1 << 28)
+    lrcc.set_plan(lrcc.KIND_LR, 28, 28, rs_level0=1)
+    try:
+        # in-place first level: 8-byte walk words + small deeper levels
+        assert 8 * (1 << 28) <= L.lrcc_workspace_query(lrcc.KIND_LR, 1 << 28, 0) < 9 * (1 << 28)
+    finally:
+        lrcc.set_plan(lrcc.KIND_LR, 28, 28, rs_level0=2)
     assert L.lrcc_workspace_query(lrcc.KIND_LR_WYLLIE, 1 << 20, 0) == 16 * (1 << 20)

@@ -24,7 +24,7 @@ def _run(src, dst, n):
     return lab.cpu().numpy()
 
 
-@pytest.fixture(params=[1, 2], ids=["hook-once", "hook-relink"])
+@pytest.fixture(params=[1, 2, 3], ids=["hook-once", "hook-relink", "hook-once-then-relink"])
 def hook(request):
     base = lrcc.get_plan(lrcc.KIND_CC, 1 << 20)["cc_hook"]
     lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=request.param)

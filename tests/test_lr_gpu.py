@@ -25,21 +25,21 @@ def _run(fn, succ, head):
 
 
 @pytest.mark.parametrize("fn", ["rs", "wyllie"])
-@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1000, 8191, 8192, 8193, 65539, 200003])
-def test_random_list_matches_oracle(fn, n):
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1000, 8191, 8192, 8193, 16385, 65539, 200003])
+def test_random_list_matches_oracle(level0, fn, n):
     for seed in (1, 2):
         succ, head = gen.list_random(n, seed)
         assert np.array_equal(_run(fn, succ, head), oracle.lr_rank(succ, head))
 
 
 @pytest.mark.parametrize("fn", ["rs", "wyllie"])
-def test_list_2p20_matches_oracle(fn):
+def test_list_2p20_matches_oracle(level0, fn):
     succ, head = workloads.lr_random(20)
     assert np.array_equal(_run(fn, succ, head), oracle.lr_rank(succ, head))
 
 
 @pytest.mark.parametrize("fn", ["rs", "wyllie"])
-def test_ordered_and_reversed_layouts(fn):
+def test_ordered_and_reversed_layouts(level0, fn):
     n = 100_003
     succ, head = gen.list_ordered(n)
     assert np.array_equal(_run(fn, succ, head), np.arange(n - 1, -1, -1))
@@ -48,7 +48,7 @@ def test_ordered_and_reversed_layouts(fn):
 
 
 @pytest.mark.parametrize("fn", ["rs", "wyllie"])
-def test_selfloop_tail_convention(fn):
+def test_selfloop_tail_convention(level0, fn):
     succ, head = gen.list_random(50_000, 3)
     tail = int(np.flatnonzero(succ == -1)[0])
     s2 = succ.copy()
@@ -56,7 +56,8 @@ def test_selfloop_tail_convention(fn):
     assert np.array_equal(_run(fn, s2, head), oracle.lr_rank(succ, head))
 
 
-def test_result_independent_of_splitters():
+@pytest.mark.parametrize("level0", [1, 2], ids=["inplace", "bucketed"])
+def test_result_independent_of_splitters(level0):
     succ, head = gen.list_random(300_000, 4)
     expect = oracle.lr_rank(succ, head)
     base = lrcc.get_plan(lrcc.KIND_LR, 300_000)
@@ -65,10 +66,23 @@ def test_result_independent_of_splitters():
             for spacing0, spacing, chains, small in ((32, 16, 2, 8192), (4, 4, 1, 1024), (256, 64, 4, 16384),
                                                      (2, 2, 2, 1024)):
                 lrcc.set_plan(lrcc.KIND_LR, 0, 32, seed=seed, rs_spacing0=spacing0, rs_spacing=spacing,
-                              rs_chains=chains, rs_small=small)
+                              rs_chains=chains, rs_small=small, rs_level0=level0)
                 assert np.array_equal(_run("rs", succ, head), expect), (seed, spacing0, spacing, chains)
     finally:
-        lrcc.set_plan(lrcc.KIND_LR, 0, 32, **{k: v for k, v in base.items()})
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, **{k: v for k, v in base.items() if k != "rs_level0"})
+        _restore_level0()
+
+
+@pytest.fixture(params=[1, 2], ids=["inplace", "bucketed"])
+def level0(request):
+    lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=request.param)
+    yield request.param
+    _restore_level0()
+
+
+def _restore_level0():
+    lrcc.set_plan(lrcc.KIND_LR, 0, 24, rs_level0=1)
+    lrcc.set_plan(lrcc.KIND_LR, 25, 32, rs_level0=2)
 
 
 def test_without_graphs_and_repeated():
@@ -89,7 +103,7 @@ def test_without_graphs_and_repeated():
 
 
 @pytest.mark.parametrize("fn", ["rs", "wyllie"])
-def test_unaligned_views(fn):
+def test_unaligned_views(level0, fn):
     # views that start one element into an allocation take the scalar paths
     succ, head = gen.list_random(70_001, 6)
     buf = torch.zeros(70_003, dtype=torch.int32, device=DEV)
@@ -102,7 +116,7 @@ def test_unaligned_views(fn):
 
 @pytest.mark.parametrize("fn", ["rs", "wyllie"])
 @pytest.mark.parametrize("case", ["cycle", "two_lists", "out_of_range", "shared_successor", "big_cycle"])
-def test_invalid_inputs_are_reported(fn, case):
+def test_invalid_inputs_are_reported(level0, fn, case):
     n = 20_000
     succ, head = gen.list_random(n, 7)
     succ = succ.copy()

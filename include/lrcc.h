@@ -97,7 +97,9 @@ lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
                      int32_t* label, void* stream);
 
 /*
- * Batched list ranking: num_lists independent lists in one launch.
+ * Batched list ranking: num_lists independent lists in one launch (a
+ * persistent kernel takes the lists from a device work queue, largest first;
+ * each list is ranked by one thread block).
  * List k owns elements [node_off[k], node_off[k+1]) of succ and rank;
  * succ values and heads[k] are LOCAL ids (0-based within list k), and the
  * ranks are local too. node_off is int64[num_lists + 1] on the device,
@@ -107,7 +109,17 @@ lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const 
                             int64_t num_lists, int32_t* rank, void* stream);
 
 /*
- * Batched connected components: num_graphs independent graphs in one launch.
+ * lr_rank_batched sizes its workspace from node_off[num_lists], which it
+ * reads back with a small copy that waits for `stream`. Callers that know
+ * the total element count pass it here instead and the call stays
+ * asynchronous (total_nodes must equal node_off[num_lists]).
+ */
+lrcc_status lr_rank_batched_sized(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
+                                  int64_t num_lists, int64_t total_nodes, int32_t* rank, void* stream);
+
+/*
+ * Batched connected components: num_graphs independent graphs in one launch
+ * (a persistent kernel, one thread block per graph, largest first).
  * Graph k owns edges [edge_off[k], edge_off[k+1]) of src/dst and vertices
  * [vert_off[k], vert_off[k+1]) of label; edge endpoints and labels are LOCAL
  * ids. Offsets are int64[num_graphs + 1] on the device, non-decreasing, 0 first.
@@ -190,7 +202,8 @@ lrcc_status lrcc_release(void* stream);
 /* Bytes of device workspace currently held by the library (all streams). */
 int64_t lrcc_workspace_bytes(void);
 
-/* Device workspace a call of the given kind and size would need. */
+/* Device workspace a call of the given kind and size would need (batched
+ * kinds: n = total elements, m = number of instances). */
 int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m);
 
 #ifdef __cplusplus

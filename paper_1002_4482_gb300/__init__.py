@@ -30,7 +30,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIME
 KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "cc_label",
-           "lr_rank_batched", "cc_label_batched", "lrcc_last_status", "lrcc_last_stats",
+           "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity")
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         lib.lr_rank_wyllie.argtypes = [p, i64, i32, p, p]
         lib.cc_label.argtypes = [p, p, i64, i64, p, p]
         lib.lr_rank_batched.argtypes = [p, p, p, i64, p, p]
+        lib.lr_rank_batched_sized.argtypes = [p, p, p, i64, i64, p, p]
         lib.cc_label_batched.argtypes = [p, p, p, p, i64, p, p]
         lib.lrcc_last_status.argtypes = [p]
         lib.lrcc_last_stats.argtypes = [p, ctypes.POINTER(Stats)]
@@ -93,7 +94,8 @@ def load() -> ctypes.CDLL:
         lib.lrcc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.lrcc_set_l2_fetch_granularity.argtypes = [i]
         lib.lrcc_get_l2_fetch_granularity.restype = i
-        for f in ("lr_rank", "lr_rank_wyllie", "cc_label", "lr_rank_batched", "cc_label_batched",
+        for f in ("lr_rank", "lr_rank_wyllie", "cc_label", "lr_rank_batched", "lr_rank_batched_sized",
+                  "cc_label_batched",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
             getattr(lib, f).restype = i
@@ -173,15 +175,18 @@ def cc_label(src: torch.Tensor, dst: torch.Tensor, n: int, out: torch.Tensor | N
 
 def lr_rank_batched(succ: torch.Tensor, node_off: torch.Tensor, heads: torch.Tensor,
                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Ranks of independent lists concatenated in ``succ`` (local ids, int64 offsets)."""
+    """Ranks of independent lists concatenated in ``succ`` (local ids, int64 offsets).
+
+    The total element count is taken from ``succ.numel()`` (it must equal
+    ``node_off[-1]``), so the call does not wait for the stream."""
     _dev_i32(succ, "succ")
     _dev_i64(node_off, "node_off")
     _dev_i32(heads, "heads")
     if node_off.numel() != heads.numel() + 1:
         raise ValueError("node_off must have len(heads) + 1 entries")
     rank = _out(out, succ.numel(), succ, "out")
-    _call(load().lr_rank_batched(succ.data_ptr(), node_off.data_ptr(), heads.data_ptr(), heads.numel(),
-                                 rank.data_ptr(), _stream(stream)), "lr_rank_batched")
+    _call(load().lr_rank_batched_sized(succ.data_ptr(), node_off.data_ptr(), heads.data_ptr(), heads.numel(),
+                                       succ.numel(), rank.data_ptr(), _stream(stream)), "lr_rank_batched")
     return rank
 
 

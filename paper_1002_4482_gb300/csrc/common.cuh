@@ -112,6 +112,11 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     return h;
 }
 
+// Offset in [0, size) of the splitter of block b (stratified splitter choice).
+__device__ __forceinline__ uint32_t block_offset(uint32_t b, uint32_t size, uint32_t seed) {
+    return static_cast<uint32_t>((static_cast<uint64_t>(mix32(b * 0x9E3779B1u + seed)) * size) >> 32);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

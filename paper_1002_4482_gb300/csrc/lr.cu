@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "block_wyllie.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -29,49 +30,9 @@ constexpr int FINAL_THREADS = 1024;
 
 // ------------------------------------------------------- shared-memory Wyllie
 
-// Wyllie's pointer jumping on val/nxt arrays held in shared memory by one
-// block of FINAL_THREADS threads (Sec. 3.1: the single-kernel variant using
-// __syncthreads). On return val[j] = sum of val over j and every element
-// after it. Rounds are capped at ceil(log2 r) + 2; a list that still has
-// links then must contain a cycle, which is recorded as invalid input.
 template <int PER>
-__device__ void cta_wyllie(int* val, int* nxt, int r, DevCtl* ctl) {
-    const int tid = threadIdx.x;
-    int cap = 2;
-    while ((1 << (cap - 2)) < r) ++cap;
-    for (int round = 0;; ++round) {
-        int nv[PER], nn[PER];
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int j = tid + q * FINAL_THREADS;
-            nv[q] = 0;
-            nn[q] = (int)NIL;
-            if (j < r) {
-                const int x = nxt[j];
-                nv[q] = val[j];
-                if (x != (int)NIL) {
-                    nv[q] += val[x];
-                    nn[q] = nxt[x];
-                    any = true;
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int j = tid + q * FINAL_THREADS;
-            if (j < r) {
-                val[j] = nv[q];
-                nxt[j] = nn[q];
-            }
-        }
-        if (!__syncthreads_or(any)) break;
-        if (round >= cap) {
-            if (tid == 0) record_error(ctl, LRCC_ERR_INVALID_INPUT, -2);
-            break;
-        }
-    }
+__device__ __forceinline__ void cta_wyllie(int* val, int* nxt, int r, DevCtl* ctl) {
+    block_wyllie<PER, FINAL_THREADS>(val, nxt, r, ctl);
 }
 
 // One block ranks a whole list of n <= PER * FINAL_THREADS elements.
@@ -126,9 +87,6 @@ __global__ void __launch_bounds__(FINAL_THREADS, 1)
 // and no compaction is needed. The head's block takes the head as its
 // splitter, and block numbers are rotated so that the head is splitter 0.
 // Offsets come from the MurmurHash3 finaliser of (block, seed).
-__device__ __forceinline__ uint32_t block_offset(uint32_t b, uint32_t size, uint32_t seed) {
-    return static_cast<uint32_t>((static_cast<uint64_t>(mix32(b * 0x9E3779B1u + seed)) * size) >> 32);
-}
 
 // Level-0 select: one streaming pass packs succ into walk words
 // W[i] = (next | SPL, splitter index) for splitters, (next, weight 1) for the

@@ -308,20 +308,37 @@ lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
     return st;
 }
 
-lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
-                            int64_t num_lists, int32_t* rank, void* stream) {
-    if (num_lists < 0) return LRCC_ERR_ARG;
+lrcc_status lr_rank_batched_sized(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
+                                  int64_t num_lists, int64_t total_nodes, int32_t* rank, void* stream) {
+    if (num_lists < 0 || total_nodes < 0) return LRCC_ERR_ARG;
     if (num_lists == 0) return LRCC_OK;
-    if (!node_off || !heads) return LRCC_ERR_ARG;
+    if (!node_off || !heads || (total_nodes > 0 && (!succ || !rank))) return LRCC_ERR_ARG;
     Ctx* c = nullptr;
     lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     const Plan p = plan_for(KIND_LR_BATCH, 0);
+    st = ensure_ws(c, lr_batched_ws(total_nodes, num_lists));
+    if (st != LRCC_OK) return st;
     reset_ctl(c, c->stream);
-    st = lr_batched_run(c, succ, node_off, heads, num_lists, rank, p);
+    st = lr_batched_run(c, succ, node_off, heads, num_lists, rank, total_nodes, p);
     c->last_kind = KIND_LR_BATCH;
     return st;
+}
+
+lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
+                            int64_t num_lists, int32_t* rank, void* stream) {
+    if (num_lists < 0) return LRCC_ERR_ARG;
+    if (num_lists == 0) return LRCC_OK;
+    if (!node_off || !heads) return LRCC_ERR_ARG;
+    // the workspace is sized from the total element count, node_off[num_lists]
+    int64_t total = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&total, node_off + num_lists, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LRCC_ERR_CUDA;
+    if (total < 0) return LRCC_ERR_ARG;
+    return lr_rank_batched_sized(succ, node_off, heads, num_lists, total, rank, stream);
 }
 
 lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
@@ -334,6 +351,8 @@ lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     const Plan p = plan_for(KIND_CC_BATCH, 0);
+    st = ensure_ws(c, cc_batched_ws(num_graphs));
+    if (st != LRCC_OK) return st;
     reset_ctl(c, c->stream);
     st = cc_batched_run(c, src, dst, edge_off, vert_off, num_graphs, label, p);
     c->last_kind = KIND_CC_BATCH;
@@ -497,8 +516,8 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
         }
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
         case KIND_CC: return 0;
-        case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n);
-        case KIND_CC_BATCH: return (int64_t)cc_batched_ws(n);
+        case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n, m);   // n = total elements, m = lists
+        case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m);      // m = graphs
         default: return -1;
     }
 }

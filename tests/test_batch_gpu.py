@@ -1,0 +1,124 @@
+"""Batched list ranking and components: every instance of a batch must equal
+the oracle on that instance alone (bit-exact)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1002_4482_gb300 as lrcc
+from gen import workloads
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def _lists(sizes, seed):
+    succ, off, heads = gen.list_batch(np.asarray(sizes, np.int64), seed)
+    rank = lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                                torch.from_numpy(heads).to(DEV))
+    lrcc.check()
+    return succ, off, heads, rank.cpu().numpy()
+
+
+def _graphs(vsizes, seed, deg=2):
+    src, dst, eoff, voff = gen.er_batch(np.asarray(vsizes, np.int64), deg, 1, seed)
+    lab = lrcc.cc_label_batched(torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV),
+                                torch.from_numpy(eoff).to(DEV), torch.from_numpy(voff).to(DEV))
+    lrcc.check()
+    return src, dst, eoff, voff, lab.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_list_batch_mixed_sizes(seed):
+    # one-block path (<= 8192), in-block ruling set (> 8192), tiny and ragged sizes
+    sizes = [1, 2, 3, 31, 33, 1000, 8191, 8192, 8193, 9000, 20000, 65537, 300000] + \
+        gen.loguniform_sizes(60, 0, 17, seed).tolist()
+    succ, off, heads, rank = _lists(sizes, seed)
+    assert np.array_equal(rank, oracle.lr_rank_batched(succ, off, heads))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_graph_batch_mixed_sizes(seed):
+    # shared-memory path (<= 16384 vertices) and global path, degree 4 and 0.5
+    sizes = [1, 2, 5, 100, 16383, 16384, 16385, 50000, 200000] + gen.loguniform_sizes(60, 0, 17, seed).tolist()
+    for deg in (2, 1):
+        src, dst, eoff, voff, lab = _graphs(sizes, seed, deg)
+        assert np.array_equal(lab, oracle.cc_batched(src, dst, eoff, voff))
+
+
+def test_batch_with_empty_instances():
+    sizes = [0, 5, 0, 0, 10000, 0]
+    succ, off, heads, rank = _lists(sizes, 3)
+    expect = oracle.lr_rank_batched(succ, off, heads)
+    assert np.array_equal(rank, expect)
+    src, dst, eoff, voff, lab = _graphs([0, 3, 0, 20000], 4)
+    assert np.array_equal(lab, oracle.cc_batched(src, dst, eoff, voff))
+
+
+def test_batch_result_equals_single_calls():
+    sizes = gen.loguniform_sizes(24, 8, 16, 9)
+    succ, off, heads, rank = _lists(sizes, 9)
+    for k in range(len(sizes)):
+        b, e = off[k], off[k + 1]
+        single = lrcc.lr_rank(torch.from_numpy(succ[b:e].copy()).to(DEV), int(heads[k])).cpu().numpy()
+        assert np.array_equal(rank[b:e], single)
+    src, dst, eoff, voff, lab = _graphs(sizes, 10)
+    for k in range(len(sizes)):
+        eb, ee, vb, ve = eoff[k], eoff[k + 1], voff[k], voff[k + 1]
+        single = lrcc.cc_label(torch.from_numpy(src[eb:ee].copy()).to(DEV),
+                               torch.from_numpy(dst[eb:ee].copy()).to(DEV), int(ve - vb)).cpu().numpy()
+        assert np.array_equal(lab[vb:ve], single)
+
+
+def test_invalid_instance_is_reported():
+    sizes = [100, 20000, 50]
+    succ, off, heads = gen.list_batch(np.asarray(sizes, np.int64), 5)
+    succ = succ.copy()
+    b = off[1]
+    tail = b + int(np.flatnonzero(succ[b:off[2]] == -1)[0])
+    succ[tail] = heads[1]                      # list 1 becomes a cycle
+    lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                         torch.from_numpy(heads).to(DEV))
+    assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+    heads2 = heads.copy()
+    heads2[2] = 50                             # head outside its list
+    succ, off, _ = gen.list_batch(np.asarray(sizes, np.int64), 5)
+    lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                         torch.from_numpy(heads2).to(DEV))
+    assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+    src, dst, eoff, voff = gen.er_batch(np.asarray([10, 10], np.int64), 2, 1, 6)
+    dst = dst.copy()
+    dst[25] = 10                               # endpoint outside graph 1
+    lrcc.cc_label_batched(torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV),
+                          torch.from_numpy(eoff).to(DEV), torch.from_numpy(voff).to(DEV))
+    assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+
+
+def test_plain_entry_point_reads_total_itself():
+    # lr_rank_batched (not _sized) takes the total from node_off on the device
+    import ctypes
+    sizes = [7, 9000, 3]
+    succ, off, heads = gen.list_batch(np.asarray(sizes, np.int64), 8)
+    s, o, h = (torch.from_numpy(x).to(DEV) for x in (succ, off, heads))
+    rank = torch.empty_like(s)
+    st = lrcc.load().lr_rank_batched(s.data_ptr(), o.data_ptr(), h.data_ptr(), len(sizes), rank.data_ptr(),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == lrcc.OK
+    lrcc.check()
+    assert np.array_equal(rank.cpu().numpy(), oracle.lr_rank_batched(succ, off, heads))
+
+
+@pytest.mark.slow
+def test_full_size_4096_batch():
+    # the batched workload: 2048 lists + 2048 graphs of degree 4, sizes log-uniform in [2^8, 2^20)
+    (succ, off, heads), (src, dst, eoff, voff) = workloads.batch(4096)
+    rank = lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                                torch.from_numpy(heads).to(DEV))
+    lab = lrcc.cc_label_batched(torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV),
+                                torch.from_numpy(eoff).to(DEV), torch.from_numpy(voff).to(DEV))
+    lrcc.check()
+    assert np.array_equal(rank.cpu().numpy(), oracle.lr_rank_batched(succ, off, heads))
+    assert np.array_equal(lab.cpu().numpy(), oracle.cc_batched(src, dst, eoff, voff))

@@ -78,6 +78,25 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
 lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
 
 /*
+ * List ranking for callers that cannot allocate device memory: code whose
+ * device memory is fixed up front (a framework that owns the allocator, a
+ * service that only uses memory reserved at start-up, a loop where a
+ * cudaMalloc could stall or fail). There is no counterpart in the paper; it
+ * is lr_rank's method with its scratch in a fixed file-scope device array.
+ *
+ * Same arguments as lr_rank, with n <= 2^20 (larger n returns LRCC_ERR_ARG
+ * at once). The call allocates nothing. Its scratch (about 10 MiB) is held by
+ * every GPU that loads the library, until the process exits; the first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * and should be made before any stream capture. All calls on a device share
+ * the array, so calls whose work overlaps on the GPU race: order them (one
+ * stream). An input that is not a single list sets rank[head] = -1 (the
+ * stream's status word is not used). Returns LRCC_ERR_ARG while phase timing
+ * (lrcc_set_timing) is on, because timing creates CUDA events.
+ */
+lrcc_status lr_rank_noalloc(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
+
+/*
  * Connected components (Sec. 4, Algorithm 4, after Shiloach and Vishkin) of
  * an undirected graph given as an edge list.
  *

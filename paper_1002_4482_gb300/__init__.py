@@ -29,7 +29,7 @@ _lib = None
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(7)
 KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 
-SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "cc_label",
+SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
            "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
@@ -75,6 +75,7 @@ def load() -> ctypes.CDLL:
         lib.lrcc_version.restype = i
         lib.lr_rank.argtypes = [p, i64, i32, p, p]
         lib.lr_rank_wyllie.argtypes = [p, i64, i32, p, p]
+        lib.lr_rank_noalloc.argtypes = [p, i64, i32, p, p]
         lib.cc_label.argtypes = [p, p, i64, i64, p, p]
         lib.lr_rank_batched.argtypes = [p, p, p, i64, p, p]
         lib.lr_rank_batched_sized.argtypes = [p, p, p, i64, i64, p, p]
@@ -94,7 +95,8 @@ def load() -> ctypes.CDLL:
         lib.lrcc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.lrcc_set_l2_fetch_granularity.argtypes = [i]
         lib.lrcc_get_l2_fetch_granularity.restype = i
-        for f in ("lr_rank", "lr_rank_wyllie", "cc_label", "lr_rank_batched", "lr_rank_batched_sized",
+        for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_batched",
+                  "lr_rank_batched_sized",
                   "cc_label_batched",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
@@ -157,6 +159,17 @@ def lr_rank_wyllie(succ: torch.Tensor, head: int, out: torch.Tensor | None = Non
     rank = _out(out, succ.numel(), succ, "out")
     _call(load().lr_rank_wyllie(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), _stream(stream)),
           "lr_rank_wyllie")
+    return rank
+
+
+def lr_rank_noalloc(succ: torch.Tensor, head: int, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """Same ranks as :func:`lr_rank` (n <= 2^20) for callers that must not allocate device memory.
+
+    ``out`` must be given (this call allocates nothing); an invalid list sets out[head] = -1."""
+    _dev_i32(succ, "succ")
+    rank = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_rank_noalloc(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), _stream(stream)),
+          "lr_rank_noalloc")
     return rank
 
 

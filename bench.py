@@ -52,6 +52,12 @@ def parse():
     ap.add_argument("--workload", choices=["large", "small"], default="large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=400)
+    ap.add_argument("--plain-launches", action="store_true",
+                    help="launch kernels directly instead of replaying CUDA graphs (for profilers that cannot "
+                         "see kernels inside graphs with conditional nodes)")
     return ap.parse_args()
 
 
@@ -197,6 +203,130 @@ def workload_config_only(name):
     return {"workload": "lr_random_2p20+cc_er_2p20_2p22", "lr": {"n": 1 << 20}, "cc": {"n": 1 << 20, "m": 1 << 22}}
 
 
+def random_gather_peak(torch, dev, stream, log2n=28):
+    """Independent random 4-byte gathers per second from a 2^log2n array (the
+    random-access ceiling the walk is measured against), in G/s."""
+    with torch.cuda.stream(stream):
+        a = torch.arange(1 << log2n, dtype=torch.int32, device=dev)
+        idx = torch.randperm(1 << log2n, device=dev)
+        out = torch.empty_like(a)
+        for _ in range(2):
+            torch.index_select(a, 0, idx, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            torch.index_select(a, 0, idx, out=out)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    del a, idx, out
+    torch.cuda.empty_cache()
+    return (1 << log2n) / (ms / 1e3) / 1e9
+
+
+def bench_batched(lrcc, torch, dev, stream, log2_count=12):
+    """4096 instances (2048 lists + 2048 graphs of average degree 4, sizes
+    log-uniform in [2^8, 2^20)): one batched launch per kind against one
+    launch per instance on the same stream."""
+    from gen import workloads
+    (succ, off, heads), (src, dst, eoff, voff) = workloads.batch(1 << log2_count)
+    with torch.cuda.stream(stream):
+        S, O, H = (torch.from_numpy(x).to(dev) for x in (succ, off, heads))
+        SR, DS, EO, VO = (torch.from_numpy(x).to(dev) for x in (src, dst, eoff, voff))
+        rank = torch.empty_like(S)
+        lab = torch.empty(int(voff[-1]), dtype=torch.int32, device=dev)
+    stream.synchronize()
+
+    def ev(fn, reps):
+        fn()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        stream.synchronize()
+        lrcc.check(stream)
+        return a.elapsed_time(b) / reps
+
+    lr_b = ev(lambda: lrcc.lr_rank_batched(S, O, H, out=rank, stream=stream), 3)
+    cc_b = ev(lambda: lrcc.cc_label_batched(SR, DS, EO, VO, n_total=int(voff[-1]), out=lab, stream=stream), 3)
+    offs, hs, eo, vo = off.tolist(), heads.tolist(), eoff.tolist(), voff.tolist()
+
+    def per_lr():
+        for k in range(len(hs)):
+            lrcc.lr_rank(S[offs[k]:offs[k + 1]], hs[k], out=rank[offs[k]:offs[k + 1]], stream=stream)
+
+    def per_cc():
+        for k in range(len(vo) - 1):
+            lrcc.cc_label(SR[eo[k]:eo[k + 1]], DS[eo[k]:eo[k + 1]], vo[k + 1] - vo[k],
+                          out=lab[vo[k]:vo[k + 1]], stream=stream)
+
+    lr_p = ev(per_lr, 1)
+    cc_p = ev(per_cc, 1)
+    units = len(succ) + len(src)
+    return {"workload": "2048 lists + 2048 graphs (avg degree 4), sizes log-uniform [2^8, 2^20), int64 offsets",
+            "list_nodes": int(len(succ)), "graph_vertices": int(voff[-1]), "graph_edges": int(len(src)),
+            "batched_ms": {"lr": lr_b, "cc": cc_b, "total": lr_b + cc_b},
+            "per_launch_ms": {"lr": lr_p, "cc": cc_p, "total": lr_p + cc_p},
+            "speedup": (lr_p + cc_p) / (lr_b + cc_b),
+            "batched_melems_per_s": units / (lr_b + cc_b) / 1e3}
+
+
+def bench_serve(torch, count=400, seed=6):
+    """Poisson stream of mixed jobs (70 % lists / 30 % graphs of average
+    degree 8, sizes log-uniform in [2^10, 2^24)) through the continuous-
+    batching server and through one-launch-per-job FIFO: saturated (all
+    submitted at once) and at half the saturated rate."""
+    import threading
+    import gen
+    from gen import workloads
+    from paper_1002_4482_gb300 import serve
+    grid = np.unique(np.floor(2.0 ** np.arange(10, 24.01, 0.25)).astype(np.int64))
+    _, kind, size = workloads.serve_jobs(count, 1.0, seed=seed)
+    pool = {}
+
+    def get(kd, n):
+        g = int(grid[np.searchsorted(grid, n, side="right") - 1])
+        if (kd, g) not in pool:
+            if kd == 0:
+                sc, h = gen.list_random(g, g)
+                pool[(kd, g)] = (torch.from_numpy(sc).pin_memory(), h)
+            else:
+                a, b = gen.er(g, 4 * g, g)
+                pool[(kd, g)] = (torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), g)
+        return pool[(kd, g)]
+
+    jobs = [(int(k), get(int(k), int(n))) for k, n in zip(kind, size)]
+
+    def run(srv, gaps):
+        futs = []
+        t = time.perf_counter()
+        for (k, p), g in zip(jobs, gaps):
+            t += g
+            d = t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)              # releases the GIL for the scheduler thread
+            futs.append(srv.submit_list(p[0], p[1]) if k == 0 else srv.submit_graph(p[0], p[1], p[2]))
+        for f in futs:
+            f.result(timeout=600)
+        st = srv.stats()
+        srv.close()
+        return st
+
+    out = {"workload": f"{count} jobs: 70 % lists / 30 % graphs (degree 8), sizes log-uniform [2^10, 2^24); "
+                       "inputs from a pool of seeded instances on a 4-per-octave size grid",
+           "saturated": {}, "half_load": {}}
+    out["saturated"]["batched"] = run(serve.Server(0, streams=4), np.zeros(count))
+    out["saturated"]["fifo"] = run(serve.FifoServer(0), np.zeros(count))
+    lam = 0.5 * out["saturated"]["batched"]["jobs_per_s"]
+    gaps = np.random.default_rng(seed).exponential(1.0 / lam, count)
+    out["half_load"]["offered_jobs_per_s"] = lam
+    out["half_load"]["batched"] = run(serve.Server(0, streams=4), gaps)
+    out["half_load"]["fifo"] = run(serve.FifoServer(0), gaps)
+    return out
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -230,6 +360,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.plain_launches:
+        for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC):
+            lrcc.set_plan(kind, 0, 32, use_graphs=2)
     succ_h, head, src_h, dst_h, n_cc, cfg = workload(args.workload)
     n_lr, m_cc = len(succ_h), len(src_h)
     units = n_lr + m_cc
@@ -288,21 +421,34 @@ def main():
 
     hbm, peak_kind = peaks()
     roofline = None
+    level0 = lrcc.get_plan(lrcc.KIND_LR, n_lr)["rs_level0"]
     if "rs_walk0" in phases:
         wt, wl = phases["rs_walk0"]
         per_launch_ms = wt / wl
         r1 = lr_stats["splitters"][0] if lr_stats["splitters"] else 0
-        alg_bytes = 16 * n_lr + 16 * r1
+        if level0 == 2:
+            # read succ (4 B) and write the element id (4 B) plus 1 B of chunk header per element;
+            # one 8-byte reduced-list word per splitter
+            alg_bytes, per_elem = 9 * n_lr + 8 * r1, "9 B per element (read succ, write id + chunk header) + 8 B per splitter"
+        else:
+            alg_bytes, per_elem = 16 * n_lr + 16 * r1, "16 B per element (read + write back its 8-byte word) + 16 B per splitter"
         achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
         traffic = None
         if NCU_WALK0["lr_cu_sha1"] == file_sha1(os.path.join(ROOT, "paper_1002_4482_gb300", "csrc", "lr.cu")) \
                 and args.workload == "large":
             traffic = NCU_WALK0["bytes_per_launch"]
-        roofline = {"kernel": "rs_walk (level 0)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                    "ms_per_launch": per_launch_ms,
-                    "algorithmic_bytes": "16 B per list element (read + write back its 8-byte walk word) "
-                                         "+ 16 B per splitter"}
+        gather = random_gather_peak(torch, dev, stream)
+        steps_per_s = n_lr / (per_launch_ms / 1e3) / 1e9
+        roofline = {"kernel": "rs_walk0c (first-level sublist walk)" if level0 == 2 else "rs_walk (first level)",
+                    "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": traffic, "ms_per_launch": per_launch_ms,
+                    "algorithmic_bytes": per_elem,
+                    "random_access": {
+                        "achieved_g_steps_per_s": steps_per_s, "peak_g_per_s": gather,
+                        "peak_kind": "measured here: torch index_select of 2^28 random 4-byte elements",
+                        "frac": steps_per_s / gather,
+                        "note": "each walk step is one dependent random read of succ; HBM row activations, "
+                                "not bytes, bound random access"}}
 
     # ordered control and Wyllie baseline on the same list size (not part of the step)
     extra = {}
@@ -376,6 +522,16 @@ def main():
                "kind": "oracle", "sample": sample[5], "seconds": t, "lr_seconds": tl, "cc_seconds": tc,
                "host_cores": os.cpu_count()}
 
+    batched = serving = None
+    if rank == 0 and not args.no_batched:
+        del rank_out, label, src, dst, succ
+        torch.cuda.empty_cache()
+        batched = bench_batched(lrcc, torch, dev, stream)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_serve:
+        serving = bench_serve(torch, args.serve_jobs)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         cfg.update({"l2": "inputs larger than L2 (4n B list, 8m B edges); no flush between steps",
                     "parallelism": f"replicas x{world}", "stream": "one non-default stream",
@@ -392,6 +548,7 @@ def main():
                        "problem_bytes_frac": (8 * m_cc + 4 * n_cc) / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
                        "rounds": cc_stats["rounds"]},
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+                "batched": batched, "serving": serving,
                 **extra}
         print(json.dumps(line), flush=True)
     if world > 1:

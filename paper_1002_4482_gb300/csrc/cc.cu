@@ -6,10 +6,11 @@
 //             have different parents, atomicMin links the larger root below
 //             the smaller one (priority write in place of the paper's
 //             "arbitrary" concurrent write);
-//   shortcut  pointer jumping until every tree is a star (SV steps 1a / 4);
 //   control   a one-thread kernel reads the change flag (SV step 5, raised by
 //             one warp-ballot store per warp) and sets the condition of a
-//             CUDA-graph while-node, so the loop runs without the host.
+//             CUDA-graph while-node, so the loop runs without the host;
+//   shortcut  pointer jumping until every tree is a star (SV steps 1a / 4),
+//             skipped after the final pass that joined nothing.
 // Links always point from a larger id to a smaller one, so no cycle can form
 // and every root is the smallest id of its tree; when a pass finds no edge
 // between two trees the trees are the components and the roots their
@@ -111,20 +112,54 @@ __device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b,
 // Hook pass. mode 1: single hooks every pass; mode 2: relink every pass;
 // mode 3: single hooks in the first pass (cheap while every tree is a
 // singleton), relink afterwards.
+//
+// Edges of a pass come from the input (first passes) or from an active-edge
+// buffer: from the second pass on, an edge whose endpoints already share a
+// parent (after the previous shortcut, a root) can never join two trees
+// again, because trees only merge; the others are appended, one warp-wide
+// atomic per 128 edges, to the buffer the next pass reads. In the first pass
+// every parent is still the vertex itself, so the parents are not read.
+struct ActiveEdges {
+    int2* buf[2];      // active buffers 1 and 2 (edge = (u, v))
+    int64_t cap;       // edges each buffer holds; 0 = no compaction
+};
+
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK)
     cc_hook(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-            int32_t* parent, int64_t n, int mode, DevCtl* ctl) {
+            int32_t* parent, int64_t n, int mode, ActiveEdges act, DevCtl* ctl) {
     const uint64_t stream_pol = policy_evict_first();
     const uint64_t keep = policy_evict_last();
-    const bool relink = mode == 2 || (mode == 3 && ctl->rounds > 0);
-    const int64_t ngroups = (m + 3) >> 2;
+    const int pass = ctl->rounds;
+    const bool first = pass == 0;
+    const bool relink = mode == 2 || (mode == 3 && !first);
+    const int sel = ctl->cc_src;                       // 0 = input edges, 1/2 = active buffer
+    const int out_sel = sel == 1 ? 2 : 1;
+    const bool compact = !first && act.cap > 0;
+    const int64_t me = sel == 0 ? m : min((int64_t)ctl->cc_count[sel], act.cap);
+    const int2* in = sel == 0 ? nullptr : act.buf[sel - 1];
+    int2* out = act.cap > 0 ? act.buf[out_sel - 1] : nullptr;
+    const int lane = threadIdx.x & 31;
+    const int64_t ngroups = (me + 3) >> 2;
     bool changed = false;
-    for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
-         g += static_cast<int64_t>(gridDim.x) * BLOCK) {
+    // warp-uniform trip count so that the warp-wide append can use full masks
+    const int64_t warp_base = (static_cast<int64_t>(blockIdx.x) * BLOCK + (threadIdx.x & ~31));
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * BLOCK;
+    for (int64_t gb = warp_base; gb < ngroups; gb += stride) {
+        const int64_t g = gb + lane;
         const int64_t e0 = g * 4;
         int u[4], v[4];
-        if (VEC && e0 + 3 < m) {
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ok[q] = e0 + q < me;
+        if (sel != 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int2 e = ok[q] ? __ldcs(in + e0 + q) : make_int2(0, 0);
+                u[q] = e.x;
+                v[q] = e.y;
+            }
+        } else if (VEC && e0 + 3 < me) {
             const int4 a = ld_stream_v4(src + e0, stream_pol);
             const int4 b = ld_stream_v4(dst + e0, stream_pol);
             u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
@@ -132,13 +167,13 @@ __global__ void __launch_bounds__(BLOCK)
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                u[q] = e0 + q < m ? ld_stream(src + e0 + q, stream_pol) : 0;
-                v[q] = e0 + q < m ? ld_stream(dst + e0 + q, stream_pol) : 0;
+                u[q] = ok[q] ? ld_stream(src + e0 + q, stream_pol) : 0;
+                v[q] = ok[q] ? ld_stream(dst + e0 + q, stream_pol) : 0;
             }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (u[q] < 0 || u[q] >= n || v[q] < 0 || v[q] >= n) {
+            if (ok[q] && (u[q] < 0 || u[q] >= n || v[q] < 0 || v[q] >= n)) {
                 record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)(e0 + q));
                 u[q] = v[q] = 0;
             }
@@ -149,16 +184,44 @@ __global__ void __launch_bounds__(BLOCK)
             a[q] = ld_hint(parent + u[q], keep);
             b[q] = ld_hint(parent + v[q], keep);
         }
+        int keep_cnt = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) changed |= hook_pair(parent, a[q], b[q], relink, keep);
+        for (int q = 0; q < 4; ++q) {
+            const bool active = ok[q] && a[q] != b[q];
+            if (active) changed |= hook_pair(parent, a[q], b[q], relink, keep);
+            keep_cnt += active;
+            ok[q] = active;
+        }
+        if (compact) {
+            int incl = keep_cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            int base = 0;
+            if (lane == 31 && total) base = atomicAdd(&ctl->cc_count[out_sel], total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            int64_t at = (int64_t)base + incl - keep_cnt;
+            if (total && base + total > act.cap && lane == 31) ctl->cc_overflow = 1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (ok[q]) {
+                    if (at < act.cap) out[at] = make_int2(u[q], v[q]);
+                    ++at;
+                }
+        }
     }
-    if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) ctl->flag = 1;
+    if (__any_sync(0xffffffffu, changed) && lane == 0) ctl->flag = 1;
 }
 
 // Pointer jumping to stars: parent[v] <- root(v). Roots do not move during
 // this pass and every value read is an ancestor, so one pass suffices.
 template <bool VEC>
-__global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n) {
+__global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n, const DevCtl* ctl) {
+    // runs after the loop control: a pass that joined nothing left every tree a star
+    if (ctl->cc_stop) return;
     const uint64_t keep = policy_evict_last();
     const int64_t ngroups = (n + 3) >> 2;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
@@ -192,9 +255,22 @@ __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n)
     }
 }
 
+// After a pass: choose the next pass's edges (the active buffer this pass
+// filled, unless it overflowed or this was the first pass) and clear that
+// buffer's successor for appends.
+__device__ __forceinline__ void next_edges(DevCtl* ctl, bool compacting) {
+    const int sel = ctl->cc_src;
+    const int out_sel = sel == 1 ? 2 : 1;
+    int next = 0;
+    if (compacting && ctl->rounds > 1 && !ctl->cc_overflow) next = out_sel;
+    ctl->cc_overflow = 0;
+    ctl->cc_src = next;
+    ctl->cc_count[next == 1 ? 2 : 1] = 0;
+}
+
 // Loop control on the device: continue while the last hook pass joined
 // something, the round cap is not reached and no error was recorded.
-__global__ void cc_control(DevCtl* ctl, cudaGraphConditionalHandle h, int cap) {
+__global__ void cc_control(DevCtl* ctl, cudaGraphConditionalHandle h, int cap, bool compacting) {
     const int r = ++ctl->rounds;
     const int f = ctl->flag;
     ctl->flag = 0;
@@ -204,11 +280,13 @@ __global__ void cc_control(DevCtl* ctl, cudaGraphConditionalHandle h, int cap) {
         cont = 0;
     }
     if (ctl->status) cont = 0;
+    next_edges(ctl, compacting);
+    ctl->cc_stop = !cont;
     cudaGraphSetConditional(h, cont);
 }
 
 // Same decision for the host-driven loop: the answer is left in ctl->pad[0].
-__global__ void cc_control_host(DevCtl* ctl, int cap) {
+__global__ void cc_control_host(DevCtl* ctl, int cap, bool compacting) {
     const int r = ++ctl->rounds;
     const int f = ctl->flag;
     ctl->flag = 0;
@@ -218,6 +296,8 @@ __global__ void cc_control_host(DevCtl* ctl, int cap) {
         cont = 0;
     }
     if (ctl->status) cont = 0;
+    next_edges(ctl, compacting);
+    ctl->cc_stop = !cont;
     ctl->pad[0] = cont;
 }
 
@@ -230,10 +310,12 @@ struct CcArgs {
     int32_t* label;
     int mode;
     int cap;
+    ActiveEdges act;
 };
 
-// Enqueues one round body: hook, shortcut (control is added by the caller).
-lrcc_status enqueue_round(Ctx* c, cudaStream_t s, const CcArgs& a) {
+// Enqueues one round's hook pass, and (separately) its shortcut pass; the
+// loop control runs between them.
+lrcc_status enqueue_hook(Ctx* c, cudaStream_t s, const CcArgs& a) {
     const bool ve = aligned16(a.src) && aligned16(a.dst);
     const bool vn = aligned16(a.label);
     const void* hk = ve ? (const void*)cc_hook<true> : (const void*)cc_hook<false>;
@@ -242,17 +324,22 @@ lrcc_status enqueue_round(Ctx* c, cudaStream_t s, const CcArgs& a) {
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((eg + BLOCK - 1) / BLOCK,
                                                                   persistent_grid(c, hk, BLOCK)));
         phase_begin(c, s);
-        if (ve) cc_hook<true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, c->ctl);
-        else cc_hook<false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, c->ctl);
+        if (ve) cc_hook<true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, a.act, c->ctl);
+        else cc_hook<false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, a.act, c->ctl);
         phase_end(c, s, PH_CC_HOOK);
     }
+    return cuda_status(cudaGetLastError());
+}
+
+lrcc_status enqueue_shortcut(Ctx* c, cudaStream_t s, const CcArgs& a) {
+    const bool vn = aligned16(a.label);
     const void* sk = vn ? (const void*)cc_shortcut<true> : (const void*)cc_shortcut<false>;
     const int64_t ng = (a.n + 3) / 4;
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((ng + BLOCK - 1) / BLOCK,
                                                               persistent_grid(c, sk, BLOCK)));
     phase_begin(c, s);
-    if (vn) cc_shortcut<true><<<g, BLOCK, 0, s>>>(a.label, a.n);
-    else cc_shortcut<false><<<g, BLOCK, 0, s>>>(a.label, a.n);
+    if (vn) cc_shortcut<true><<<g, BLOCK, 0, s>>>(a.label, a.n, c->ctl);
+    else cc_shortcut<false><<<g, BLOCK, 0, s>>>(a.label, a.n, c->ctl);
     phase_end(c, s, PH_CC_SHORTCUT);
     return cuda_status(cudaGetLastError());
 }
@@ -282,8 +369,9 @@ lrcc_status build_loop_graph(Ctx* c, const CcArgs& a, cudaGraphExec_t* out) {
         cudaGraphDestroy(g);
         return LRCC_ERR_CUDA;
     }
-    st = enqueue_round(c, c->capture, a);
-    cc_control<<<1, 1, 0, c->capture>>>(c->ctl, h, a.cap);
+    st = enqueue_hook(c, c->capture, a);
+    cc_control<<<1, 1, 0, c->capture>>>(c->ctl, h, a.cap, a.act.cap > 0);
+    if (st == LRCC_OK) st = enqueue_shortcut(c, c->capture, a);
     cudaGraph_t captured = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c->capture, &captured);
     if (st == LRCC_OK && ce != cudaSuccess) st = LRCC_ERR_CUDA;
@@ -295,9 +383,23 @@ lrcc_status build_loop_graph(Ctx* c, const CcArgs& a, cudaGraphExec_t* out) {
 
 }  // namespace
 
+// Active-edge buffers: each holds an eighth of the edges (a pass that keeps
+// more falls back to the full edge list); none for small graphs.
+int64_t cc_active_cap(int64_t m) { return m >= (int64_t(1) << 16) ? m / 8 : 0; }
+size_t cc_ws(int64_t m) {
+    const int64_t cap = cc_active_cap(m);
+    return cap > 0 ? 2 * align_up(sizeof(int2) * (size_t)cap, 256) : 0;
+}
+
 lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
                    int32_t* label, const Plan& p) {
-    CcArgs a{src, dst, m, n, label, std::min(std::max(p.cc_hook, 1), 3), 0};
+    CcArgs a{src, dst, m, n, label, std::min(std::max(p.cc_hook, 1), 3), 0, ActiveEdges{}};
+    const int64_t acap = cc_active_cap(m);
+    if (acap > 0 && c->ws_bytes >= cc_ws(m)) {
+        a.act.buf[0] = static_cast<int2*>(c->ws);
+        a.act.buf[1] = reinterpret_cast<int2*>(static_cast<char*>(c->ws) + align_up(sizeof(int2) * (size_t)acap, 256));
+        a.act.cap = acap;
+    }
     int lg = 0;
     while ((int64_t(1) << lg) < n) ++lg;
     a.cap = p.cc_max_rounds > 0 ? p.cc_max_rounds : 64 + 4 * lg;
@@ -313,7 +415,8 @@ lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, in
 
     if (p.use_graphs != 2) {
         const std::vector<uint64_t> key = {(uint64_t)KIND_CC, (uint64_t)src, (uint64_t)dst, (uint64_t)m,
-                                           (uint64_t)n, (uint64_t)label, (uint64_t)a.mode, (uint64_t)a.cap};
+                                           (uint64_t)n, (uint64_t)label, (uint64_t)a.mode, (uint64_t)a.cap,
+                                           (uint64_t)a.act.buf[0], (uint64_t)a.act.cap};
         GraphEntry* e = nullptr;
         for (auto& ge : c->graphs)
             if (ge.key == key) e = &ge;
@@ -343,9 +446,11 @@ lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, in
     if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) return LRCC_ERR_NOMEM;
     lrcc_status st = LRCC_OK;
     for (int r = 0; r < a.cap + 1; ++r) {
-        st = enqueue_round(c, s, a);
+        st = enqueue_hook(c, s, a);
         if (st != LRCC_OK) break;
-        cc_control_host<<<1, 1, 0, s>>>(c->ctl, a.cap);
+        cc_control_host<<<1, 1, 0, s>>>(c->ctl, a.cap, a.act.cap > 0);
+        st = enqueue_shortcut(c, s, a);
+        if (st != LRCC_OK) break;
         cudaMemcpyAsync(host_flag, &c->ctl->pad[0], sizeof(int), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             st = LRCC_ERR_CUDA;

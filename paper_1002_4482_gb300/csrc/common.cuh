@@ -23,7 +23,11 @@ struct DevCtl {
     int ovf_next;        // read-only walk: overflow chunks claimed
     int pairs;           // read-only walk: (element, rank) pairs produced
     int place_next;      // read-only walk: next pair slice to place
-    int pad[7];
+    int cc_src;          // component loop: edges of the next pass (0 = input, 1/2 = active buffer)
+    int cc_count[3];     // component loop: edges appended to active buffer 1 / 2
+    int cc_overflow;     // component loop: an active buffer was too small
+    int cc_stop;         // component loop: the last pass joined nothing
+    int pad[1];
 };
 
 __device__ __forceinline__ void record_error(DevCtl* c, int code, int where = -1) {

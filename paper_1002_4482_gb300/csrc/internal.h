@@ -115,6 +115,8 @@ size_t lr_wyllie_ws(int64_t n, const Plan& p);
 // --- connected components (cc.cu)
 lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
                    int32_t* label, const Plan& p);
+int64_t cc_active_cap(int64_t m);
+size_t cc_ws(int64_t m);
 
 // --- batched (batch.cu)
 lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, const int32_t* heads,

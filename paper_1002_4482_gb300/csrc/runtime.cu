@@ -302,6 +302,8 @@ lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     const Plan p = plan_for(KIND_CC, n);
+    st = ensure_ws(c, cc_ws(m));
+    if (st != LRCC_OK) return st;
     reset_ctl(c, c->stream);
     st = cc_run(c, src, dst, m, n, label, p);
     c->last_kind = KIND_CC;
@@ -515,7 +517,7 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
             return n > p.rs_small ? (int64_t)rs_layout(n, p, 152 * 8).bytes : 0;
         }
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
-        case KIND_CC: return 0;
+        case KIND_CC: return (int64_t)cc_ws(m);
         case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n, m);   // n = total elements, m = lists
         case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m);      // m = graphs
         default: return -1;

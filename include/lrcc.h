@@ -148,6 +148,15 @@ lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64
                              void* stream);
 
 /*
+ * cc_label_batched reads edge_off[num_graphs] back (a small copy that waits
+ * for `stream`) to size its buffers; with the total edge count given here
+ * the call stays asynchronous (total_edges must equal edge_off[num_graphs]).
+ */
+lrcc_status cc_label_batched_sized(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
+                                   const int64_t* vert_off, int64_t num_graphs, int64_t total_edges,
+                                   int32_t* label, void* stream);
+
+/*
  * Waits for `stream`, then returns and clears the device status word of its
  * workspace (LRCC_OK if nothing was recorded since the last call).
  */
@@ -222,7 +231,8 @@ lrcc_status lrcc_release(void* stream);
 int64_t lrcc_workspace_bytes(void);
 
 /* Device workspace a call of the given kind and size would need (batched
- * kinds: n = total elements, m = number of instances). */
+ * lists: n = total elements, m = lists; batched graphs: n = total edges,
+ * m = graphs). */
 int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m);
 
 #ifdef __cplusplus

@@ -30,7 +30,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIME
 KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
-           "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "lrcc_last_status", "lrcc_last_stats",
+           "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "cc_label_batched_sized", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity")
@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
         lib.lr_rank_batched.argtypes = [p, p, p, i64, p, p]
         lib.lr_rank_batched_sized.argtypes = [p, p, p, i64, i64, p, p]
         lib.cc_label_batched.argtypes = [p, p, p, p, i64, p, p]
+        lib.cc_label_batched_sized.argtypes = [p, p, p, p, i64, i64, p, p]
         lib.lrcc_last_status.argtypes = [p]
         lib.lrcc_last_stats.argtypes = [p, ctypes.POINTER(Stats)]
         lib.lrcc_set_plan.argtypes = [i, i, i, ctypes.POINTER(Plan)]
@@ -97,7 +98,7 @@ def load() -> ctypes.CDLL:
         lib.lrcc_get_l2_fetch_granularity.restype = i
         for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_batched",
                   "lr_rank_batched_sized",
-                  "cc_label_batched",
+                  "cc_label_batched", "cc_label_batched_sized",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
             getattr(lib, f).restype = i
@@ -215,8 +216,9 @@ def cc_label_batched(src: torch.Tensor, dst: torch.Tensor, edge_off: torch.Tenso
     if n_total is None:
         n_total = int(vert_off[-1].item())
     label = _out(out, n_total, src, "out")
-    _call(load().cc_label_batched(src.data_ptr(), dst.data_ptr(), edge_off.data_ptr(), vert_off.data_ptr(),
-                                  vert_off.numel() - 1, label.data_ptr(), _stream(stream)), "cc_label_batched")
+    _call(load().cc_label_batched_sized(src.data_ptr(), dst.data_ptr(), edge_off.data_ptr(), vert_off.data_ptr(),
+                                        vert_off.numel() - 1, src.numel(), label.data_ptr(), _stream(stream)),
+          "cc_label_batched")
     return label
 
 

@@ -12,13 +12,20 @@
 //           splitter list held and ranked in shared memory, then the expand.
 //   graphs  up to SMEM_ELEMS * 2 vertices: the parent array lives in shared
 //           memory, hooks follow both ends to their roots and re-link until
-//           joined; larger: the parent array is the instance's label slice in
-//           global memory and hooks are single atomicMin links. Rounds of
-//           hooking and shortcutting repeat until __syncthreads_or sees no
-//           edge between two trees (Sec. 4, Algorithm 4, step 5).
+//           joined; up to CC_LARGE vertices: the parent array is the
+//           instance's label slice in global memory and hooks are single
+//           atomicMin links. Rounds of hooking and shortcutting repeat until
+//           __syncthreads_or sees no edge between two trees (Sec. 4,
+//           Algorithm 4, step 5).
+// Graphs above CC_LARGE vertices would keep one block busy far longer than
+// the rest of the batch, so they are labelled together instead, as one
+// disjoint union in global ids (voff[k] + local id), by grid-wide hook and
+// shortcut kernels looped on the device; components never cross instances,
+// so the union's min-id labels minus voff[k] are each instance's labels.
 #include <algorithm>
 
 #include "block_wyllie.cuh"
+#include "cc_device.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -32,6 +39,8 @@ constexpr int PER = SMEM_ELEMS / BT;      // per-thread share in block_wyllie
 constexpr int CC_SMEM_VERTS = 2 * SMEM_ELEMS;
 constexpr size_t SMEM_BYTES = 2 * sizeof(int) * SMEM_ELEMS;   // 64 KB, both kinds
 constexpr int NCLASS = 33;
+constexpr int64_t CC_LARGE = int64_t(1) << 15;   // graphs above this many vertices go to the union path
+constexpr int SEG_BLOCK = 256;
 
 // Order instances by size class (floor(log2 size)), largest first.
 __global__ void __launch_bounds__(1024)
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(BT)
         const int64_t k = order[q];
         const int64_t eb = eoff[k], m = eoff[k + 1] - eb;
         const int64_t vb = voff[k], n = voff[k + 1] - vb;
-        if (n <= 0 || m < 0 || n > 0x7FFFFFFELL) continue;
+        if (n <= 0 || m < 0 || n > 0x7FFFFFFELL || n > CC_LARGE) continue;
         int lg = 0;
         while ((int64_t(1) << lg) < n) ++lg;
         const int cap = max_rounds > 0 ? max_rounds : 64 + 4 * lg;
@@ -314,6 +323,289 @@ __global__ void __launch_bounds__(BT)
             graph_in_smem(src + eb, dst + eb, m, (int)n, label + vb, sm, cap, ctl);
         else
             graph_in_global(src + eb, dst + eb, m, n, label + vb, cap, ctl);
+    }
+}
+
+// ---------------------------------------------------- graphs: the union path
+
+// The large instances, in instance order, with prefix sums of their edge and
+// vertex counts; nlarge = their number. One block.
+struct LargeSet {
+    int32_t* ids;
+    int64_t* lep;   // [nlarge + 1] edge prefix
+    int64_t* lvp;   // [nlarge + 1] vertex prefix
+    int* nlarge;
+};
+
+__device__ __forceinline__ int64_t block_exclusive_scan64(int64_t v, int64_t* s_tmp, int64_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_tmp[wid] = incl;
+    __syncthreads();
+    int64_t off = 0, all = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        off += w < wid ? s_tmp[w] : 0;
+        all += s_tmp[w];
+    }
+    __syncthreads();
+    *total = all;
+    return off + incl - v;
+}
+
+__global__ void __launch_bounds__(1024)
+    large_prep(const int64_t* __restrict__ eoff, const int64_t* __restrict__ voff, int64_t count, LargeSet L) {
+    __shared__ int64_t s_tmp[32];
+    const int64_t per = (count + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = min(count, b + per);
+    auto large = [&](int64_t k) {
+        const int64_t n = voff[k + 1] - voff[k], m = eoff[k + 1] - eoff[k];
+        return n > CC_LARGE && n <= 0x7FFFFFFELL && m >= 0;
+    };
+    int64_t c = 0, me = 0, mv = 0;
+    for (int64_t k = b; k < e; ++k)
+        if (large(k)) {
+            ++c;
+            me += eoff[k + 1] - eoff[k];
+            mv += voff[k + 1] - voff[k];
+        }
+    int64_t tc, te, tv;
+    int64_t at = block_exclusive_scan64(c, s_tmp, &tc);
+    int64_t ae = block_exclusive_scan64(me, s_tmp, &te);
+    int64_t av = block_exclusive_scan64(mv, s_tmp, &tv);
+    for (int64_t k = b; k < e; ++k)
+        if (large(k)) {
+            L.ids[at] = (int32_t)k;
+            L.lep[at] = ae;
+            L.lvp[at] = av;
+            ++at;
+            ae += eoff[k + 1] - eoff[k];
+            av += voff[k + 1] - voff[k];
+        }
+    if (threadIdx.x == 0) {
+        *L.nlarge = (int)tc;
+        L.lep[tc] = te;
+        L.lvp[tc] = tv;
+    }
+}
+
+// Largest i with pre[i] <= x, over pre[0..nl] (pre[0] = 0, x < pre[nl]).
+__device__ __forceinline__ int seg_find(const int64_t* pre, int nl, int64_t x) {
+    int lo = 0, hi = nl;   // invariant: pre[lo] <= x < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int SEG_RUN = 8;   // consecutive vertices or edges per thread
+
+// label[g] = g for every vertex g of a large instance (g = voff[k] + local).
+__global__ void __launch_bounds__(SEG_BLOCK) seg_init(LargeSet L, const int64_t* __restrict__ voff, int32_t* label) {
+    const int nl = *L.nlarge;
+    const int64_t V = L.lvp[nl];
+    for (int64_t x0 = ((int64_t)blockIdx.x * SEG_BLOCK + threadIdx.x) * SEG_RUN; x0 < V;
+         x0 += (int64_t)gridDim.x * SEG_BLOCK * SEG_RUN) {
+        int i = seg_find(L.lvp, nl, x0);
+        for (int64_t x = x0; x < min(x0 + SEG_RUN, V); ++x) {
+            while (x >= L.lvp[i + 1]) ++i;
+            const int64_t g = voff[L.ids[i]] + (x - L.lvp[i]);
+            label[g] = (int32_t)g;
+        }
+    }
+}
+
+// One hook pass over the large instances (single atomicMin hooks with a read
+// before the atomic, as in the single-instance path). The first two passes
+// read the instances' edges (local ids, instance found by binary search);
+// from the second pass on, edges still joining two trees are appended as
+// global (u, v) pairs to the active buffer that the next pass reads instead.
+struct SegActive {
+    int2* buf[2];
+    int64_t cap;
+};
+
+// Blocks take slices of the pass's edges from a counter, in order, so the
+// edges in flight belong to a few consecutive graphs and their parent
+// entries stay in L2 (a grid-stride loop would let blocks drift across many
+// graphs, whose parent arrays together are far larger than L2).
+constexpr int SEG_SLICE = SEG_BLOCK * 64;
+
+__global__ void __launch_bounds__(SEG_BLOCK)
+    seg_hook(LargeSet L, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+             const int64_t* __restrict__ eoff, const int64_t* __restrict__ voff, int32_t* label, SegActive act,
+             DevCtl* ctl) {
+    __shared__ int s_slice;
+    const uint64_t keep = policy_evict_last();
+    const uint64_t stream_pol = policy_evict_first();
+    const int nl = *L.nlarge;
+    const int sel = ctl->cc_src;
+    const int out_sel = sel == 1 ? 2 : 1;
+    const bool compact = ctl->rounds > 0 && act.cap > 0;
+    const int64_t E = sel == 0 ? L.lep[nl] : min((int64_t)ctl->cc_count[sel], act.cap);
+    const int lane = threadIdx.x & 31;
+    bool changed = false;
+    for (;;) {
+        if (threadIdx.x == 0) s_slice = atomicAdd(&ctl->seg_next, 1);
+        __syncthreads();
+        const int64_t start = (int64_t)s_slice * SEG_SLICE;
+        __syncthreads();
+        if (start >= E) break;
+        const int64_t end = min(start + SEG_SLICE, E);
+        int i = 0;
+        if (sel == 0 && start + threadIdx.x < end) i = seg_find(L.lep, nl, start + threadIdx.x);
+        for (int64_t c0 = start; c0 < end; c0 += (int64_t)SEG_BLOCK * SEG_RUN) {
+            int32_t u[SEG_RUN], v[SEG_RUN];
+#pragma unroll
+            for (int q = 0; q < SEG_RUN; ++q) {
+                u[q] = v[q] = -1;
+                const int64_t e = c0 + (int64_t)q * SEG_BLOCK + threadIdx.x;   // coalesced across the block
+                if (e >= end) continue;
+                if (sel != 0) {
+                    const int2 x = __ldcs(act.buf[sel - 1] + e);
+                    u[q] = x.x;
+                    v[q] = x.y;
+                } else {
+                    while (e >= L.lep[i + 1]) ++i;
+                    const int k = L.ids[i];
+                    const int64_t at = eoff[k] + (e - L.lep[i]);
+                    const int64_t base = voff[k], n = voff[k + 1] - base;
+                    const int a = ld_stream(src + at, stream_pol), b = ld_stream(dst + at, stream_pol);
+                    if (a < 0 || a >= n || b < 0 || b >= n) {
+                        record_error(ctl, LRCC_ERR_INVALID_INPUT, k);
+                        continue;
+                    }
+                    u[q] = (int32_t)(base + a);
+                    v[q] = (int32_t)(base + b);
+                }
+            }
+            int32_t pa[SEG_RUN], pb[SEG_RUN];
+#pragma unroll
+            for (int q = 0; q < SEG_RUN; ++q) {
+                pa[q] = u[q] >= 0 ? ld_hint(label + u[q], keep) : 0;
+                pb[q] = u[q] >= 0 ? ld_hint(label + v[q], keep) : 0;
+            }
+            int nkeep = 0;
+#pragma unroll
+            for (int q = 0; q < SEG_RUN; ++q) {
+                const bool active = u[q] >= 0 && pa[q] != pb[q];
+                if (active) changed |= hook_pair(label, pa[q], pb[q], false, keep);
+                if (!active) u[q] = -1;
+                nkeep += active;
+            }
+            if (compact) {
+                int incl = nkeep;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                int base = 0;
+                if (lane == 31 && total) base = atomicAdd(&ctl->cc_count[out_sel], total);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                if (lane == 31 && total && (int64_t)base + total > act.cap) ctl->cc_overflow = 1;
+                int64_t at = (int64_t)base + incl - nkeep;
+                int2* out = act.buf[out_sel - 1];
+#pragma unroll
+                for (int q = 0; q < SEG_RUN; ++q)
+                    if (u[q] >= 0) {
+                        if (at < act.cap) out[at] = make_int2(u[q], v[q]);
+                        ++at;
+                    }
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) ctl->flag = 1;
+}
+
+__global__ void seg_control(DevCtl* ctl, cudaGraphConditionalHandle h, int cap, bool compacting) {
+    const int r = ++ctl->rounds;
+    const int f = ctl->flag;
+    ctl->flag = 0;
+    unsigned cont = f != 0;
+    if (cont && r >= cap) {
+        record_error(ctl, LRCC_ERR_NOT_CONVERGED, r);
+        cont = 0;
+    }
+    if (ctl->status) cont = 0;
+    ctl->cc_stop = !cont;
+    // next pass: the active buffer this pass filled (from the second pass on)
+    const int sel = ctl->cc_src;
+    const int out_sel = sel == 1 ? 2 : 1;
+    int next = 0;
+    if (compacting && r > 1 && !ctl->cc_overflow) next = out_sel;
+    ctl->cc_overflow = 0;
+    ctl->cc_src = next;
+    ctl->cc_count[next == 1 ? 2 : 1] = 0;
+    ctl->seg_next = 0;
+    ctl->seg_next_v = 0;
+    cudaGraphSetConditional(h, cont);
+}
+
+// The same decision for a host-driven loop (plain launches): answer in ctl->pad[0].
+__global__ void seg_control_host(DevCtl* ctl, int cap, bool compacting) {
+    const int r = ++ctl->rounds;
+    const int f = ctl->flag;
+    ctl->flag = 0;
+    int cont = f != 0;
+    if (cont && r >= cap) {
+        record_error(ctl, LRCC_ERR_NOT_CONVERGED, r);
+        cont = 0;
+    }
+    if (ctl->status) cont = 0;
+    ctl->cc_stop = !cont;
+    const int sel = ctl->cc_src;
+    const int out_sel = sel == 1 ? 2 : 1;
+    int next = 0;
+    if (compacting && r > 1 && !ctl->cc_overflow) next = out_sel;
+    ctl->cc_overflow = 0;
+    ctl->cc_src = next;
+    ctl->cc_count[next == 1 ? 2 : 1] = 0;
+    ctl->seg_next = 0;
+    ctl->seg_next_v = 0;
+    ctl->pad[0] = cont;
+}
+
+// Pointer jumping to stars over the large instances' vertices (skipped after
+// the pass that joined nothing); with finalize, global labels become local.
+template <bool FINALIZE>
+__global__ void __launch_bounds__(SEG_BLOCK)
+    seg_shortcut(LargeSet L, const int64_t* __restrict__ voff, int32_t* label, DevCtl* ctl) {
+    __shared__ int s_slice;
+    if (!FINALIZE && ctl->cc_stop) return;
+    const uint64_t keep = policy_evict_last();
+    const int nl = *L.nlarge;
+    const int64_t V = L.lvp[nl];
+    int* counter = FINALIZE ? &ctl->seg_next : &ctl->seg_next_v;
+    for (;;) {
+        if (threadIdx.x == 0) s_slice = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t start = (int64_t)s_slice * SEG_SLICE;
+        __syncthreads();
+        if (start >= V) break;
+        const int64_t end = min(start + SEG_SLICE, V);
+        int i = start + threadIdx.x < end ? seg_find(L.lvp, nl, start + threadIdx.x) : 0;
+        for (int64_t x = start + threadIdx.x; x < end; x += SEG_BLOCK) {
+            while (x >= L.lvp[i + 1]) ++i;
+            const int64_t base = voff[L.ids[i]];
+            const int64_t g = base + (x - L.lvp[i]);
+            if (FINALIZE) {
+                label[g] = (int32_t)(label[g] - base);
+            } else {
+                const int p = label[g];
+                if (p != g) {
+                    const int r = find_root(label, p, keep);
+                    if (r != p) label[g] = r;
+                }
+            }
+        }
     }
 }
 
@@ -328,7 +620,15 @@ size_t lr_batched_ws(int64_t total_nodes, int64_t count) {
            align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(count, 1), 256);
 }
 
-size_t cc_batched_ws(int64_t count) { return align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(count, 1), 256); }
+// Active-edge buffers of the union path: an eighth of all edges each.
+int64_t cc_batched_active_cap(int64_t total_edges) { return total_edges >= (int64_t(1) << 16) ? total_edges / 8 : 0; }
+
+size_t cc_batched_ws(int64_t count, int64_t total_edges) {
+    const size_t c = (size_t)std::max<int64_t>(count, 1);
+    const int64_t acap = cc_batched_active_cap(total_edges);
+    return 2 * align_up(sizeof(int32_t) * c, 256) + 2 * align_up(sizeof(int64_t) * (c + 1), 256) + 256 +
+           (acap > 0 ? 2 * align_up(sizeof(int2) * (size_t)acap, 256) : 0);
+}
 
 lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, const int32_t* heads, int64_t count,
                            int32_t* rank, int64_t total_nodes, const Plan& p) {
@@ -350,12 +650,114 @@ lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, cons
 }
 
 lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const int64_t* eoff, const int64_t* voff,
-                           int64_t count, int32_t* label, const Plan& p) {
+                           int64_t count, int64_t total_edges, int32_t* label, const Plan& p) {
     cudaStream_t s = c->stream;
-    int32_t* order = static_cast<int32_t*>(c->ws);
+    const size_t cnt = (size_t)std::max<int64_t>(count, 1);
+    char* w = static_cast<char*>(c->ws);
+    int32_t* order = reinterpret_cast<int32_t*>(w);
+    w += align_up(sizeof(int32_t) * cnt, 256);
+    LargeSet L;
+    L.ids = reinterpret_cast<int32_t*>(w);
+    w += align_up(sizeof(int32_t) * cnt, 256);
+    L.lep = reinterpret_cast<int64_t*>(w);
+    w += align_up(sizeof(int64_t) * (cnt + 1), 256);
+    L.lvp = reinterpret_cast<int64_t*>(w);
+    w += align_up(sizeof(int64_t) * (cnt + 1), 256);
+    L.nlarge = reinterpret_cast<int*>(w);
+    w += 256;
+    SegActive act{{nullptr, nullptr}, cc_batched_active_cap(total_edges)};
+    if (act.cap > 0) {
+        act.buf[0] = reinterpret_cast<int2*>(w);
+        act.buf[1] = reinterpret_cast<int2*>(w + align_up(sizeof(int2) * (size_t)act.cap, 256));
+    }
+
     phase_begin(c, s);
     batch_order<<<1, 1024, 0, s>>>(voff, eoff, nullptr, count, order, c->ctl);
+    large_prep<<<1, 1024, 0, s>>>(eoff, voff, count, L);
     phase_end(c, s, PH_BATCH_PREP);
+
+    // the union of the large graphs: init, device-side loop, finalize
+    const int gs = persistent_grid(c, (const void*)seg_hook, SEG_BLOCK);
+    const int gv = persistent_grid(c, (const void*)seg_shortcut<false>, SEG_BLOCK);
+    const int cap = 64 + 4 * 31;
+    phase_begin(c, s);
+    seg_init<<<gv, SEG_BLOCK, 0, s>>>(L, voff, label);
+    if (p.use_graphs == 2) {
+        // host-driven loop, one flag read per pass (so profilers see every kernel)
+        int* host_flag = nullptr;
+        if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) return LRCC_ERR_NOMEM;
+        lrcc_status st = LRCC_OK;
+        for (int r = 0; r <= cap; ++r) {
+            seg_hook<<<gs, SEG_BLOCK, 0, s>>>(L, src, dst, eoff, voff, label, act, c->ctl);
+            seg_control_host<<<1, 1, 0, s>>>(c->ctl, cap, act.cap > 0);
+            seg_shortcut<false><<<gv, SEG_BLOCK, 0, s>>>(L, voff, label, c->ctl);
+            cudaMemcpyAsync(host_flag, &c->ctl->pad[0], sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) {
+                st = LRCC_ERR_CUDA;
+                break;
+            }
+            if (!*host_flag) break;
+        }
+        cudaFreeHost(host_flag);
+        if (st != LRCC_OK) return st;
+    } else {
+    const std::vector<uint64_t> key = {(uint64_t)KIND_CC_BATCH, (uint64_t)src, (uint64_t)dst, (uint64_t)eoff,
+                                       (uint64_t)voff, (uint64_t)count, (uint64_t)label, (uint64_t)c->ws,
+                                       (uint64_t)act.cap};
+    GraphEntry* e = nullptr;
+    for (auto& ge : c->graphs)
+        if (ge.key == key) e = &ge;
+    if (!e) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        lrcc_status st = LRCC_OK;
+        cudaGraphConditionalHandle h;
+        cudaGraphNode_t node;
+        cudaGraphNodeParams cp = {};
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) return LRCC_ERR_CUDA;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) st = LRCC_ERR_CUDA;
+        if (st == LRCC_OK) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) st = LRCC_ERR_CUDA;
+        }
+        if (st == LRCC_OK) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(c->capture, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                st = LRCC_ERR_CUDA;
+            } else {
+                seg_hook<<<gs, SEG_BLOCK, 0, c->capture>>>(L, src, dst, eoff, voff, label, act, c->ctl);
+                seg_control<<<1, 1, 0, c->capture>>>(c->ctl, h, cap, act.cap > 0);
+                seg_shortcut<false><<<gv, SEG_BLOCK, 0, c->capture>>>(L, voff, label, c->ctl);
+                cudaGraph_t captured = nullptr;
+                if (cudaStreamEndCapture(c->capture, &captured) != cudaSuccess) st = LRCC_ERR_CUDA;
+            }
+        }
+        if (st == LRCC_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) st = LRCC_ERR_CUDA;
+        cudaGraphDestroy(g);
+        if (st != LRCC_OK) {
+            cudaGetLastError();
+            return st;
+        }
+        if (c->graphs.size() >= 16) {
+            auto it = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                       [](const GraphEntry& x, const GraphEntry& y) { return x.last_use < y.last_use; });
+            cudaGraphExecDestroy(it->exec);
+            c->graphs.erase(it);
+        }
+        c->graphs.push_back(GraphEntry{key, ex, 0});
+        e = &c->graphs.back();
+    }
+    e->last_use = ++c->tick;
+    if (cudaGraphLaunch(e->exec, s) != cudaSuccess) return LRCC_ERR_CUDA;
+    }
+    seg_shortcut<true><<<gv, SEG_BLOCK, 0, s>>>(L, voff, label, c->ctl);
+    phase_end(c, s, PH_CC_LOOP);
+
+    // every other graph: one block each, largest first
     lrcc_status st = set_smem((const void*)cc_batch_kernel);
     if (st != LRCC_OK) return st;
     const int g = (int)std::min<int64_t>(count, persistent_grid(c, (const void*)cc_batch_kernel, BT, SMEM_BYTES));

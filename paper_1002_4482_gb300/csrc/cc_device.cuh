@@ -1,0 +1,69 @@
+// Device functions of the component kernels (hooking and root finding),
+// shared by the single-instance and batched paths.
+#pragma once
+
+#include "common.cuh"
+
+namespace lrcc {
+
+// Follow parents to a root. Every link goes to a smaller id, so the walk
+// ends within n steps on any state the kernels can produce.
+__device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t x, uint64_t keep) {
+    for (;;) {
+        const int32_t p = ld_cg_hint(parent + x, keep);
+        if (p == x) return x;
+        x = p;
+    }
+}
+
+// Root of x with path halving: each visited element is re-pointed to its
+// grandparent. The store may race with an atomicMin on the same element;
+// either value is an ancestor, and a link that such a store replaces is
+// re-made by the thread whose atomicMin saw it (it goes on to join the old
+// parent with its smaller root), so no connection is lost.
+__device__ __forceinline__ int32_t find_root_halving(int32_t* parent, int32_t x, uint64_t keep) {
+    int32_t p = ld_cg_hint(parent + x, keep);
+    while (p != x) {
+        const int32_t g = ld_cg_hint(parent + p, keep);
+        if (g == p) return p;
+        parent[x] = g;
+        x = g;
+        p = ld_cg_hint(parent + x, keep);
+    }
+    return x;
+}
+
+// One edge whose endpoints currently have parents a and b.
+//  relink = false: a single atomicMin links the larger parent below the
+//                  smaller one (one Shiloach-Vishkin style hook);
+//  relink = true:  both ends are followed to their roots; when the atomicMin
+//                  finds the larger root already linked below `old` by
+//                  another thread, the join continues with (old, smaller
+//                  root), so the edge's endpoints share a tree when it returns.
+// Returns whether a link was written.
+__device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b, bool relink, uint64_t keep) {
+    if (a == b) return false;
+    if (!relink) {
+        // Read before the atomic: on hubs most hooks find the parent already
+        // at or below `lo`, and skipping those keeps same-address atomics
+        // from serialising in L2.
+        const int32_t hi = max(a, b), lo = min(a, b);
+        if (ld_cg_hint(parent + hi, keep) > lo) atomicMin(parent + hi, lo);
+        return true;
+    }
+    bool linked = false;
+    for (;;) {
+        a = find_root_halving(parent, a, keep);
+        b = find_root_halving(parent, b, keep);
+        if (a == b) return linked;
+        const int32_t hi = max(a, b), lo = min(a, b);
+        const int32_t old = atomicMin(parent + hi, lo);
+        linked = true;
+        if (old == hi) return true;
+        // hi had been linked below `old` by another thread: join old and lo
+        a = old;
+        b = lo;
+    }
+}
+
+}  // namespace lrcc

@@ -27,7 +27,9 @@ struct DevCtl {
     int cc_count[3];     // component loop: edges appended to active buffer 1 / 2
     int cc_overflow;     // component loop: an active buffer was too small
     int cc_stop;         // component loop: the last pass joined nothing
-    int pad[1];
+    int seg_next;        // batched union path: next edge slice of the current pass
+    int seg_next_v;      // batched union path: next vertex slice of the current shortcut
+    int pad[3];
 };
 
 __device__ __forceinline__ void record_error(DevCtl* c, int code, int where = -1) {

@@ -122,9 +122,9 @@ size_t cc_ws(int64_t m);
 lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, const int32_t* heads,
                            int64_t count, int32_t* rank, int64_t total_nodes, const Plan& p);
 lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const int64_t* eoff,
-                           const int64_t* voff, int64_t count, int32_t* label, const Plan& p);
+                           const int64_t* voff, int64_t count, int64_t total_edges, int32_t* label, const Plan& p);
 size_t lr_batched_ws(int64_t total_nodes, int64_t count);
-size_t cc_batched_ws(int64_t count);
+size_t cc_batched_ws(int64_t count, int64_t total_edges);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -343,22 +343,38 @@ lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const 
     return lr_rank_batched_sized(succ, node_off, heads, num_lists, total, rank, stream);
 }
 
-lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
-                             const int64_t* vert_off, int64_t num_graphs, int32_t* label, void* stream) {
-    if (num_graphs < 0) return LRCC_ERR_ARG;
+lrcc_status cc_label_batched_sized(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
+                                   const int64_t* vert_off, int64_t num_graphs, int64_t total_edges,
+                                   int32_t* label, void* stream) {
+    if (num_graphs < 0 || total_edges < 0) return LRCC_ERR_ARG;
     if (num_graphs == 0) return LRCC_OK;
-    if (!edge_off || !vert_off) return LRCC_ERR_ARG;
+    if (!edge_off || !vert_off || !label || (total_edges > 0 && (!src || !dst))) return LRCC_ERR_ARG;
     Ctx* c = nullptr;
     lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     const Plan p = plan_for(KIND_CC_BATCH, 0);
-    st = ensure_ws(c, cc_batched_ws(num_graphs));
+    st = ensure_ws(c, cc_batched_ws(num_graphs, total_edges));
     if (st != LRCC_OK) return st;
     reset_ctl(c, c->stream);
-    st = cc_batched_run(c, src, dst, edge_off, vert_off, num_graphs, label, p);
+    st = cc_batched_run(c, src, dst, edge_off, vert_off, num_graphs, total_edges, label, p);
     c->last_kind = KIND_CC_BATCH;
     return st;
+}
+
+lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
+                             const int64_t* vert_off, int64_t num_graphs, int32_t* label, void* stream) {
+    if (num_graphs < 0) return LRCC_ERR_ARG;
+    if (num_graphs == 0) return LRCC_OK;
+    if (!edge_off || !vert_off) return LRCC_ERR_ARG;
+    // the active-edge buffers are sized from the total edge count, edge_off[num_graphs]
+    int64_t total = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&total, edge_off + num_graphs, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LRCC_ERR_CUDA;
+    if (total < 0) return LRCC_ERR_ARG;
+    return cc_label_batched_sized(src, dst, edge_off, vert_off, num_graphs, total, label, stream);
 }
 
 lrcc_status lrcc_last_status(void* stream) {
@@ -519,7 +535,7 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
         case KIND_CC: return (int64_t)cc_ws(m);
         case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n, m);   // n = total elements, m = lists
-        case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m);      // m = graphs
+        case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m, n);   // n = total edges, m = graphs
         default: return -1;
     }
 }

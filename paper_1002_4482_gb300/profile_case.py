@@ -29,7 +29,7 @@ def main(argv):
     what, log2 = argv[0], int(argv[1])
     variant = argv[2] if len(argv) > 2 else ""
     dev = torch.device("cuda:0")
-    for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC):
+    for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC, lrcc.KIND_LR_BATCH, lrcc.KIND_CC_BATCH):
         lrcc.set_plan(kind, 0, 32, use_graphs=2)
     if variant == "inplace":
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=1)

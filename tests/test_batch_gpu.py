@@ -122,3 +122,15 @@ def test_full_size_4096_batch():
     lrcc.check()
     assert np.array_equal(rank.cpu().numpy(), oracle.lr_rank_batched(succ, off, heads))
     assert np.array_equal(lab.cpu().numpy(), oracle.cc_batched(src, dst, eoff, voff))
+
+
+def test_plain_graph_entry_point_reads_total_itself():
+    import ctypes
+    src, dst, eoff, voff = gen.er_batch(np.asarray([100, 40000, 70000, 3], np.int64), 2, 1, 12)
+    a, b, eo, vo = (torch.from_numpy(x).to(DEV) for x in (src, dst, eoff, voff))
+    lab = torch.empty(int(voff[-1]), dtype=torch.int32, device=DEV)
+    st = lrcc.load().cc_label_batched(a.data_ptr(), b.data_ptr(), eo.data_ptr(), vo.data_ptr(), 4, lab.data_ptr(),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == lrcc.OK
+    lrcc.check()
+    assert np.array_equal(lab.cpu().numpy(), oracle.cc_batched(src, dst, eoff, voff))

@@ -109,9 +109,9 @@ __device__ void list_in_smem(const int32_t* succ, int n, int head, int32_t* rank
 // Rank one larger list with a ruling set inside the block; W is the list's
 // slice of the 8-byte word workspace.
 __device__ void list_ruling_set(const int32_t* succ, int64_t n, int head, int32_t* rank, uint64_t* W,
-                                int* val, int* nxt, int* s_work, uint32_t seed, DevCtl* ctl) {
-    // spacing: a power of two with at most SMEM_ELEMS splitters
-    int logD = 2;
+                                int* val, int* nxt, int* s_work, uint32_t seed, int min_logD, DevCtl* ctl) {
+    // spacing: a power of two, at least 2^min_logD, with at most SMEM_ELEMS splitters
+    int logD = max(2, min_logD);
     while (((n + (int64_t(1) << logD) - 1) >> logD) > SMEM_ELEMS) ++logD;
     const int64_t D = int64_t(1) << logD;
     const int r = (int)((n + D - 1) >> logD);
@@ -191,7 +191,7 @@ __device__ void list_ruling_set(const int32_t* succ, int64_t n, int head, int32_
 __global__ void __launch_bounds__(BT)
     lr_batch_kernel(const int32_t* __restrict__ succ, const int64_t* __restrict__ off, const int32_t* __restrict__ heads,
                     int64_t count, const int32_t* __restrict__ order, int32_t* __restrict__ rank, uint64_t* W,
-                    uint32_t seed, DevCtl* ctl) {
+                    uint32_t seed, int min_logD, DevCtl* ctl) {
     extern __shared__ int sm[];
     int* val = sm;
     int* nxt = sm + SMEM_ELEMS;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(BT)
         if (n <= SMEM_ELEMS)
             list_in_smem(succ + b, (int)n, head, rank + b, val, nxt, ctl);
         else
-            list_ruling_set(succ + b, n, head, rank + b, W + b, val, nxt, &s_work, seed ^ (uint32_t)k, ctl);
+            list_ruling_set(succ + b, n, head, rank + b, W + b, val, nxt, &s_work, seed ^ (uint32_t)k, min_logD, ctl);
     }
 }
 
@@ -440,8 +440,9 @@ constexpr int SEG_SLICE = SEG_BLOCK * 64;
 __global__ void __launch_bounds__(SEG_BLOCK)
     seg_hook(LargeSet L, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
              const int64_t* __restrict__ eoff, const int64_t* __restrict__ voff, int32_t* label, SegActive act,
-             DevCtl* ctl) {
+             int mode, DevCtl* ctl) {
     __shared__ int s_slice;
+    const bool relink = mode == 2 || (mode == 3 && ctl->rounds > 0);
     const uint64_t keep = policy_evict_last();
     const uint64_t stream_pol = policy_evict_first();
     const int nl = *L.nlarge;
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(SEG_BLOCK)
 #pragma unroll
             for (int q = 0; q < SEG_RUN; ++q) {
                 const bool active = u[q] >= 0 && pa[q] != pb[q];
-                if (active) changed |= hook_pair(label, pa[q], pb[q], false, keep);
+                if (active) changed |= hook_pair(label, pa[q], pb[q], relink, keep);
                 if (!active) u[q] = -1;
                 nkeep += active;
             }
@@ -643,8 +644,10 @@ lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, cons
     if (st != LRCC_OK) return st;
     const int g = (int)std::min<int64_t>(count, persistent_grid(c, (const void*)lr_batch_kernel, BT, SMEM_BYTES));
     phase_begin(c, s);
+    int min_logD = 2;
+    while (min_logD < 20 && (1 << (min_logD + 1)) <= p.rs_spacing0) ++min_logD;
     lr_batch_kernel<<<g, BT, SMEM_BYTES, s>>>(succ, off, heads, count, order, rank, W,
-                                              (uint32_t)(p.seed ^ (p.seed >> 32)), c->ctl);
+                                              (uint32_t)(p.seed ^ (p.seed >> 32)), min_logD, c->ctl);
     phase_end(c, s, PH_LR_BATCH);
     return cuda_status(cudaGetLastError());
 }
@@ -688,7 +691,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
         if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) return LRCC_ERR_NOMEM;
         lrcc_status st = LRCC_OK;
         for (int r = 0; r <= cap; ++r) {
-            seg_hook<<<gs, SEG_BLOCK, 0, s>>>(L, src, dst, eoff, voff, label, act, c->ctl);
+            seg_hook<<<gs, SEG_BLOCK, 0, s>>>(L, src, dst, eoff, voff, label, act, p.cc_hook, c->ctl);
             seg_control_host<<<1, 1, 0, s>>>(c->ctl, cap, act.cap > 0);
             seg_shortcut<false><<<gv, SEG_BLOCK, 0, s>>>(L, voff, label, c->ctl);
             cudaMemcpyAsync(host_flag, &c->ctl->pad[0], sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -703,7 +706,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
     } else {
     const std::vector<uint64_t> key = {(uint64_t)KIND_CC_BATCH, (uint64_t)src, (uint64_t)dst, (uint64_t)eoff,
                                        (uint64_t)voff, (uint64_t)count, (uint64_t)label, (uint64_t)c->ws,
-                                       (uint64_t)act.cap};
+                                       (uint64_t)act.cap, (uint64_t)p.cc_hook};
     GraphEntry* e = nullptr;
     for (auto& ge : c->graphs)
         if (ge.key == key) e = &ge;
@@ -729,7 +732,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
                                               cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
                 st = LRCC_ERR_CUDA;
             } else {
-                seg_hook<<<gs, SEG_BLOCK, 0, c->capture>>>(L, src, dst, eoff, voff, label, act, c->ctl);
+                seg_hook<<<gs, SEG_BLOCK, 0, c->capture>>>(L, src, dst, eoff, voff, label, act, p.cc_hook, c->ctl);
                 seg_control<<<1, 1, 0, c->capture>>>(c->ctl, h, cap, act.cap > 0);
                 seg_shortcut<false><<<gv, SEG_BLOCK, 0, c->capture>>>(L, voff, label, c->ctl);
                 cudaGraph_t captured = nullptr;

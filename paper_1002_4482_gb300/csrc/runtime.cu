@@ -33,13 +33,27 @@ int log2_ceil(int64_t n) {
     return l;
 }
 
+// Built-in plans: the choices of an autotune run on a GB300
+// (python -m paper_1002_4482_gb300.autotune), per size class of ceil(log2 n).
 void init_plans_locked() {
     if (g_plan_init) return;
     for (int k = 0; k < 6; ++k)
         for (int l = 0; l <= 32; ++l) {
-            g_plan[k][l] = Plan{};
-            // the read-only first level pays off once the list is well beyond L2
-            if (l < 25) g_plan[k][l].rs_level0 = 1;
+            Plan& p = g_plan[k][l];
+            p = Plan{};
+            p.rs_small = 16384;
+            if (l <= 18) {
+                p.rs_level0 = 1, p.rs_spacing0 = 8, p.rs_spacing = 16;
+            } else if (l <= 22) {
+                p.rs_level0 = 1, p.rs_spacing0 = 8, p.rs_spacing = 8;
+            } else if (l <= 26) {
+                p.rs_level0 = 1, p.rs_spacing0 = 16, p.rs_spacing = 8;
+            } else {
+                // the read-only first level pays off once the list is far beyond L2
+                p.rs_level0 = 2, p.rs_spacing0 = 32, p.rs_spacing = 8;
+            }
+            // batched lists: minimum spacing of the in-block ruling sets
+            if (k == KIND_LR_BATCH) p.rs_spacing0 = 64;
         }
     g_plan_init = true;
 }

@@ -69,7 +69,7 @@ def test_result_independent_of_splitters(level0):
                               rs_chains=chains, rs_small=small, rs_level0=level0)
                 assert np.array_equal(_run("rs", succ, head), expect), (seed, spacing0, spacing, chains)
     finally:
-        lrcc.set_plan(lrcc.KIND_LR, 0, 32, **{k: v for k, v in base.items() if k != "rs_level0"})
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, seed=base["seed"])
         _restore_level0()
 
 
@@ -81,8 +81,9 @@ def level0(request):
 
 
 def _restore_level0():
-    lrcc.set_plan(lrcc.KIND_LR, 0, 24, rs_level0=1)
-    lrcc.set_plan(lrcc.KIND_LR, 25, 32, rs_level0=2)
+    # the library's built-in table (see csrc/runtime.cu)
+    for lo, hi, l0, d0, d in ((0, 18, 1, 8, 16), (19, 22, 1, 8, 8), (23, 26, 1, 16, 8), (27, 32, 2, 32, 8)):
+        lrcc.set_plan(lrcc.KIND_LR, lo, hi, rs_level0=l0, rs_spacing0=d0, rs_spacing=d, rs_small=16384, rs_chains=1)
 
 
 def test_without_graphs_and_repeated():

@@ -487,15 +487,31 @@ def main():
         rank_p = torch.empty(n_lr, dtype=torch.int32).pin_memory()
         label_p = torch.empty(n_cc, dtype=torch.int32).pin_memory()
 
+        stream2 = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream2):
+            src2 = torch.empty_like(src)
+            dst2 = torch.empty_like(dst)
+            label2 = torch.empty_like(label)
+        stream2.synchronize()
+
         def e2e_step():
+            # the list half and the graph half of the step on two streams, so the
+            # edges' upload overlaps the list ranking
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            stream2.wait_event(ev)
             with torch.cuda.stream(stream):
                 succ.copy_(succ_p, non_blocking=True)
-                src.copy_(src_p, non_blocking=True)
-                dst.copy_(dst_p, non_blocking=True)
                 lrcc.lr_rank(succ, head, out=rank_out, stream=stream)
-                lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
                 rank_p.copy_(rank_out, non_blocking=True)
-                label_p.copy_(label, non_blocking=True)
+            with torch.cuda.stream(stream2):
+                src2.copy_(src_p, non_blocking=True)
+                dst2.copy_(dst_p, non_blocking=True)
+                lrcc.cc_label(src2, dst2, n_cc, out=label2, stream=stream2)
+                label_p.copy_(label2, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(stream2)
+            stream.wait_event(done)
 
         for _ in range(args.warmup):
             e2e_step()
@@ -509,11 +525,14 @@ def main():
         stream.synchronize()
         barrier()
         lrcc.check(stream)
+        lrcc.check(stream2)
         e2e_ms = max_over_ranks(a.elapsed_time(b) / args.steps)
         if rank == 0:
             assert rank_p[head].item() == n_lr - 1
         e2e = {"value": units * world / (e2e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": 4 * n_lr + 8 * m_cc, "d2h_bytes_per_step": 4 * n_lr + 4 * n_cc}
+               "h2d_bytes_per_step": 4 * n_lr + 8 * m_cc, "d2h_bytes_per_step": 4 * n_lr + 4 * n_cc,
+               "note": "pinned host buffers; list and graph halves on two streams (edge upload overlaps list ranking)"}
+        del succ_p, src_p, dst_p, rank_p, label_p, src2, dst2, label2
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -169,6 +169,8 @@ typedef struct lrcc_stats {
     int64_t splitters[8];    /* lr_rank: splitters chosen at each level */
     int32_t rounds;          /* cc_label: hook passes (including the final, quiet one) */
     int32_t jump_rounds;     /* lr_rank_wyllie: pointer-jumping rounds */
+    int64_t overflow_chunks; /* lr_rank, read-only first level: 8-element chunks that did not fit
+                                their walk block's region and went to the shared overflow pool */
 } lrcc_stats;
 lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out);
 

@@ -47,7 +47,8 @@ struct RsLayout {
     size_t off_W0 = 0;
     bool readonly = false;          // level 0 by the read-only walk (chunks, scan, scatter, place)
     int64_t grid = 0, cap = 0, ovf_cap = 0;
-    size_t off_ids = 0, off_meta = 0, off_ovf_owner = 0, off_fill = 0, off_ovf_used = 0, off_counts = 0, off_totals = 0,
+    int segcap = 0, units = 0;
+    size_t off_ids = 0, off_meta = 0, off_fill = 0, off_counts = 0, off_totals = 0,
         off_vis = 0;
     size_t bytes = 0;
 };

@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(BLOCK)
 constexpr int CIDS = 8;        // element ids per chunk (one 32-byte sector)
 constexpr int NBK_LOG = 8;
 constexpr int NBK = 1 << NBK_LOG;
+constexpr int NSEG = 4;        // scatter work units per walk block region
 
 struct Level0 {
     int64_t n, nb, bh;   // elements, splitters (blocks), the head's block
@@ -288,13 +289,13 @@ struct Level0 {
 struct Chunks {
     int32_t* ids;        // chunk c: ids[8c .. 8c+8), unused slots -1
     uint64_t* meta;      // meta[c] = k0 << 32 | j
-    int32_t* ovf_owner;  // block that wrote overflow chunk o
     int* fill;           // chunks written into each block's own region
-    int* ovf_used;       // overflow chunks each block took
-    int* counts;         // [NBK][grid] elements per (bucket, block); then row offsets
+    int* counts;         // [NBK][units] elements per (bucket, scatter unit); then row offsets
     int* totals;         // [NBK] elements per bucket
     uint32_t* vis;       // careful-mode marks, one bit per element
-    int64_t cap;         // chunks per block region
+    int64_t cap;         // chunks per block region (NSEG segments of segcap)
+    int segcap;          // chunks per segment (even); a segment is one scatter work unit
+    int units;           // scatter units: NSEG per block region, then the overflow pool's segments
     int64_t ovf_cap;     // overflow chunks
     int64_t ovf_base;    // index of the first overflow chunk (= grid * cap)
     int shift;           // coarse bucket of element x = x >> shift
@@ -329,10 +330,10 @@ __global__ void __launch_bounds__(BLOCK)
     rs_walk0c(const int32_t* __restrict__ succ, Level0 L0, Chunks C, uint64_t* __restrict__ R1, int* work,
               DevCtl* ctl) {
     constexpr int WCHUNK = 64;
-    __shared__ int s_fill, s_ovf;
-    __shared__ int s_cnt[NBK];
-    for (int t = threadIdx.x; t < NBK; t += BLOCK) s_cnt[t] = 0;
-    if (threadIdx.x == 0) s_fill = s_ovf = 0;
+    __shared__ int s_fill;
+    __shared__ int s_cnt[NSEG][NBK];
+    for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) (&s_cnt[0][0])[t] = 0;
+    if (threadIdx.x == 0) s_fill = 0;
     __syncthreads();
     const int64_t r = L0.nb;
     const int lane = threadIdx.x & 31;
@@ -422,19 +423,20 @@ __global__ void __launch_bounds__(BLOCK)
                 // flush one chunk: own region first, then the shared overflow pool
                 const int slot = atomicAdd(&s_fill, 1);
                 int64_t c = -1;
+                int ovf_unit = -1;   // scatter unit of an overflow chunk (counted in global memory)
                 if (slot < C.cap) {
                     c = (int64_t)blockIdx.x * C.cap + slot;
                 } else {
                     const int o = atomicAdd(&ctl->ovf_next, 1);
                     if (o < C.ovf_cap) {
                         c = C.ovf_base + o;
-                        C.ovf_owner[o] = blockIdx.x;
-                        atomicAdd(&s_ovf, 1);
+                        ovf_unit = (int)gridDim.x * NSEG + o / C.segcap;
                     } else {
                         record_error(ctl, LRCC_ERR_INVALID_INPUT, -4);
                     }
                 }
                 if (c >= 0) {
+                    const int seg = slot / C.segcap;
                     int32_t v[CIDS];
 #pragma unroll
                     for (int t = 0; t < CIDS; ++t) v[t] = t < bn[q] ? buf[q][t] : -1;
@@ -444,7 +446,10 @@ __global__ void __launch_bounds__(BLOCK)
                     C.meta[c] = (static_cast<uint64_t>(k0[q]) << 32) | static_cast<uint64_t>(j[q]);
 #pragma unroll
                     for (int t = 0; t < CIDS; ++t)
-                        if (t < bn[q]) atomicAdd(&s_cnt[v[t] >> C.shift], 1);
+                        if (t < bn[q]) {
+                            if (ovf_unit < 0) atomicAdd(&s_cnt[seg][v[t] >> C.shift], 1);
+                            else atomicAdd(&C.counts[(int64_t)(v[t] >> C.shift) * C.units + ovf_unit], 1);
+                        }
                 }
                 k0[q] = k[q] + 1;
                 bn[q] = 0;
@@ -459,11 +464,11 @@ __global__ void __launch_bounds__(BLOCK)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        C.fill[blockIdx.x] = min(s_fill, (int)C.cap);
-        C.ovf_used[blockIdx.x] = s_ovf;
+    if (threadIdx.x == 0) C.fill[blockIdx.x] = min(s_fill, (int)C.cap);
+    for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) {
+        const int bk = t % NBK, seg = t / NBK;
+        C.counts[(int64_t)bk * C.units + (int64_t)blockIdx.x * NSEG + seg] = s_cnt[seg][bk];
     }
-    for (int t = threadIdx.x; t < NBK; t += BLOCK) C.counts[(int64_t)t * gridDim.x + blockIdx.x] = s_cnt[t];
 }
 
 // Exclusive scan of each bucket's row of per-block counts, in place, one
@@ -505,25 +510,54 @@ __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int 
     if (threadIdx.x == SCAN_THREADS - 1) totals[blockIdx.x] = run;
 }
 
-// Chunks of block c -> (element, rank) pairs at the block's offsets of each
-// bucket. Run with the walk's grid, block c taking the walk block c's chunks.
-// Radix-partition style: each round a block loads SCAT_U chunks per thread,
-// ranks the round's pairs by bucket in shared memory, lays them out sorted
-// by bucket in a shared tile and writes every bucket's run with coalesced
-// stores at the block's next offset for that bucket.
-constexpr int SCAT_U = 2;
-constexpr int SCAT_ITEMS = SCAT_U * BLOCK * CIDS;
-__global__ void __launch_bounds__(BLOCK)
-    rs_scatter(Chunks C, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n, DevCtl* ctl) {
-    __shared__ int s_base[NBK];     // next free pair of each bucket for this block
-    __shared__ int s_hist[NBK];     // pairs of each bucket in the current round
-    __shared__ int s_tstart[NBK];   // start of each bucket's run in the tile
-    __shared__ int s_warp[BLOCK / 32];
-    __shared__ int s_items;
-    __shared__ uint64_t s_tile[SCAT_ITEMS];
+// Chunks of walk block g -> (element, rank) pairs at block g's offsets of
+// each bucket. Radix-partition style, in rounds of SC_CHUNKS chunks: the
+// round's chunk ids and headers arrive in shared memory by bulk copy (two
+// buffers, the next round in flight while this one is processed), the
+// round's elements are ranked by bucket with shared atomics, their indices
+// laid out sorted by bucket in a tile, and every bucket's run is written
+// with coalesced stores at the block's next offset for that bucket. Blocks
+// are persistent and take work units u = blockIdx.x, + gridDim.x, ...: the
+// NSEG segments of every walk block's region, then the segments of the shared
+// overflow pool (each unit's per-bucket counts come from the walk).
+constexpr int SC_CHUNKS = 2 * BLOCK;            // chunks per round, two per thread
+constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
+constexpr int SC_WAIT_LIMIT = 1 << 22;          // polls of a bulk-copy barrier before giving up
+struct ScatterSmem {
+    int32_t ids[2][SC_ITEMS];      // chunk ids of the round in each buffer
+    uint64_t meta[2][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
+    int32_t top[SC_CHUNKS];        // rank of the first element of each chunk
+    uint16_t tile[SC_ITEMS];       // slot indices sorted by bucket
+    int cnt[2][NBK];               // elements per bucket in the round (alternating)
+    int base[NBK];                 // next free pair of each bucket for this region
+    int start[NBK];                // global start of each bucket's run in the round
+    int tstart[NBK];               // start of each bucket's run in the tile
+    int warp[BLOCK / 32];
+    uint64_t bar[2];
+};
+constexpr size_t SC_SMEM = sizeof(ScatterSmem);
+
+// The 8 ids of one chunk from shared memory. Lanes 4-7 of every 8 read the
+// two 16-byte halves in the other order, so that each quarter-warp phase of
+// the 16-byte loads touches all 32 banks once.
+__device__ __forceinline__ void load_chunk(const int32_t* p, int32_t (&id)[CIDS]) {
+    const int sw = (threadIdx.x >> 2) & 1;
+    const int4* src = reinterpret_cast<const int4*>(p);
+    const int4 a = src[sw], d = src[sw ^ 1];
+    const int4 lo = sw ? d : a, hi = sw ? a : d;
+    id[0] = lo.x; id[1] = lo.y; id[2] = lo.z; id[3] = lo.w;
+    id[4] = hi.x; id[5] = hi.y; id[6] = hi.z; id[7] = hi.w;
+}
+
+__global__ void __launch_bounds__(BLOCK, 4)
+    rs_scatter(Chunks C, int G, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n,
+               DevCtl* ctl) {
+    extern __shared__ __align__(128) unsigned char sc_raw[];
+    ScatterSmem& s = *reinterpret_cast<ScatterSmem*>(sc_raw);
     static_assert(NBK == BLOCK, "one thread per bucket");
+    static_assert(SC_ITEMS <= 65536, "tile holds 16-bit slot indices");
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    // block-wide exclusive scan of one value per thread (uses s_warp; two syncs)
+    // block-wide exclusive scan of one value per thread (uses s.warp; two syncs)
     auto block_scan = [&](int v, int* total) {
         int incl = v;
 #pragma unroll
@@ -531,12 +565,12 @@ __global__ void __launch_bounds__(BLOCK)
             const int x = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += x;
         }
-        if (lane == 31) s_warp[wid] = incl;
+        if (lane == 31) s.warp[wid] = incl;
         __syncthreads();
         int off = 0, all = 0;
 #pragma unroll
         for (int w = 0; w < BLOCK / 32; ++w) {
-            const int x = s_warp[w];
+            const int x = s.warp[w];
             off += w < wid ? x : 0;
             all += x;
         }
@@ -544,81 +578,139 @@ __global__ void __launch_bounds__(BLOCK)
         *total = all;
         return off + incl - v;
     };
+    int bstart;                     // start of bucket t in the pair array
     {
         int all = 0;
-        const int start = block_scan(C.totals[t], &all);
-        if (t == 0) ctl->pairs = all;
-        s_base[t] = start + C.counts[(int64_t)t * gridDim.x + blockIdx.x];
-        s_hist[t] = 0;
+        bstart = block_scan(C.totals[t], &all);
+        if (blockIdx.x == 0 && t == 0) ctl->pairs = all;
+    }
+    s.cnt[0][t] = s.cnt[1][t] = 0;
+    if (t == 0) {
+        mbar_init(&s.bar[0], 1);
+        mbar_init(&s.bar[1], 1);
+        fence_proxy_async_smem();   // the initialised barriers are visible to the bulk copies
     }
     __syncthreads();
-    const int nf = C.fill[blockIdx.x];
-    const bool has_ovf = C.ovf_used[blockIdx.x] > 0;
-    const int64_t no = has_ovf ? min((int64_t)ctl->ovf_next, C.ovf_cap) : 0;
-    const int64_t own0 = (int64_t)blockIdx.x * C.cap;
-    const int64_t nrounds_own = (nf + SCAT_U * BLOCK - 1) / (SCAT_U * BLOCK);
-    const int64_t nrounds = nrounds_own + (no + SCAT_U * BLOCK - 1) / (SCAT_U * BLOCK);
-    for (int64_t rd = 0; rd < nrounds; ++rd) {
-        int64_t ch[SCAT_U];
+    const uint64_t pol = policy_evict_first();
+    uint32_t phase = 0;             // bit b: parity of the next completion of buffer b's barrier
+    uint32_t in_flight = 0;         // bit b: a copy into buffer b is not yet waited for (thread 0)
+    int par = 0;                    // which cnt array the next round counts in
+    bool failed = false;
+
+    // issue the bulk copy of round k of region g (chunks own0 + k*SC_CHUNKS ..) into buffer b
+    auto issue = [&](int64_t first, int nf, int k, int b) {
+        const int64_t c0 = first + (int64_t)k * SC_CHUNKS;
+        const int cnt = min(SC_CHUNKS, nf - k * SC_CHUNKS);
+        const int cm = (cnt + 1) & ~1;   // headers in pairs: 16-byte multiple (segments are even)
+        const uint32_t bi = (uint32_t)cnt * CIDS * 4u, bm = (uint32_t)cm * 8u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s.bar[b], bi + bm);
+        bulk_g2s(s.ids[b], C.ids + c0 * CIDS, bi, &s.bar[b], pol);
+        bulk_g2s(s.meta[b], C.meta + c0, bm, &s.bar[b], pol);
+        in_flight |= 1u << b;
+    };
+
+    // one round over buffer b, whose chunks [0, cnt) are valid (a chunk whose
+    // first id is -1 is empty)
+    auto process = [&](int b, int cnt) {
+        int* cntp = s.cnt[par];
+        // the owners' suffix ranks first (L2 gathers), so their latency overlaps the counting
+        int32_t top[2];
 #pragma unroll
-        for (int u = 0; u < SCAT_U; ++u) {
-            if (rd < nrounds_own) {
-                const int64_t i = rd * SCAT_U * BLOCK + u * BLOCK + t;
-                ch[u] = i < nf ? own0 + i : -1;
-            } else {
-                const int64_t o = (rd - nrounds_own) * SCAT_U * BLOCK + u * BLOCK + t;
-                ch[u] = (o < no && C.ovf_owner[o] == (int)blockIdx.x) ? C.ovf_base + o : -1;
-            }
+        for (int u = 0; u < 2; ++u) {
+            const int c = u * BLOCK + t;
+            const uint64_t mt = s.meta[b][c];
+            top[u] = (c < cnt && s.ids[b][c * CIDS] >= 0) ? __ldg(S1 + lo32(mt)) - 1 - (int32_t)hi32(mt) : 0;
         }
-        int32_t id[SCAT_U][CIDS];
-        int32_t top[SCAT_U];
+        int loc[2][CIDS];
 #pragma unroll
-        for (int u = 0; u < SCAT_U; ++u) {
-            if (ch[u] >= 0) {
-                const int4* src = reinterpret_cast<const int4*>(C.ids + ch[u] * CIDS);
-                const int4 a = __ldcs(src), b = __ldcs(src + 1);
-                id[u][0] = a.x; id[u][1] = a.y; id[u][2] = a.z; id[u][3] = a.w;
-                id[u][4] = b.x; id[u][5] = b.y; id[u][6] = b.z; id[u][7] = b.w;
-                const uint64_t mt = __ldcs(reinterpret_cast<const unsigned long long*>(C.meta + ch[u]));
-                top[u] = S1[lo32(mt)] - 1 - (int32_t)hi32(mt);
-            } else {
-#pragma unroll
-                for (int q = 0; q < CIDS; ++q) id[u][q] = -1;
-                top[u] = 0;
-            }
-        }
-        int local[SCAT_U][CIDS];
-#pragma unroll
-        for (int u = 0; u < SCAT_U; ++u)
+        for (int u = 0; u < 2; ++u) {
+            const int c = u * BLOCK + t;
+            int32_t id[CIDS];
+            load_chunk(&s.ids[b][c * CIDS], id);
 #pragma unroll
             for (int q = 0; q < CIDS; ++q)
-                local[u][q] = id[u][q] >= 0 ? atomicAdd(&s_hist[id[u][q] >> C.shift], 1) : 0;
+                loc[u][q] = (c < cnt && id[q] >= 0) ? atomicAdd(&cntp[id[q] >> C.shift], 1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) s.top[u * BLOCK + t] = top[u];
         __syncthreads();
-        const int h = s_hist[t];
+        const int h = s.cnt[par][t];
+        s.cnt[par ^ 1][t] = 0;      // counts of the next round
         int items = 0;
         const int ts = block_scan(h, &items);
-        s_tstart[t] = ts;
-        s_hist[t] = s_base[t];      // global start of this round's run of bucket t
-        s_base[t] += h;
-        if (t == 0) s_items = items;
+        s.tstart[t] = ts;
+        s.start[t] = s.base[t];
+        s.base[t] += h;
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < SCAT_U; ++u)
+        for (int u = 0; u < 2; ++u) {
+            const int c = u * BLOCK + t;
+            int32_t id[CIDS];
+            load_chunk(&s.ids[b][c * CIDS], id);
 #pragma unroll
             for (int q = 0; q < CIDS; ++q)
-                if (id[u][q] >= 0)
-                    s_tile[s_tstart[id[u][q] >> C.shift] + local[u][q]] =
-                        pack((uint32_t)id[u][q], (uint32_t)(top[u] - q));
-        __syncthreads();
-        const int ni = s_items;
-        for (int i = t; i < ni; i += BLOCK) {
-            const uint64_t pr = s_tile[i];
-            const int bk = (int)(lo32(pr) >> C.shift);
-            const int64_t pos = (int64_t)s_hist[bk] + (i - s_tstart[bk]);
-            if (pos < n) pairs[pos] = pr;
+                if (c < cnt && id[q] >= 0) s.tile[s.tstart[id[q] >> C.shift] + loc[u][q]] = (uint16_t)(c * CIDS + q);
         }
         __syncthreads();
-        s_hist[t] = 0;
+        for (int i = t; i < items; i += BLOCK) {
+            const int x = s.tile[i];
+            const int32_t id = s.ids[b][x];
+            const int bk = id >> C.shift;
+            const int64_t pos = (int64_t)s.start[bk] + (i - s.tstart[bk]);
+            if (pos < n) pairs[pos] = pack((uint32_t)id, (uint32_t)(s.top[x >> 3] - (x & 7)));
+        }
+        fence_proxy_async_smem();   // the buffer's reads come before the next bulk copy into it
+        __syncthreads();
+        par ^= 1;
+    };
+
+    const int64_t no_all = min((int64_t)ctl->ovf_next, C.ovf_cap);
+    const int own_units = G * NSEG;
+    for (int unit = blockIdx.x; unit < C.units && !failed; unit += gridDim.x) {
+        int nf;
+        int64_t c0;
+        if (unit < own_units) {
+            // segment seg of walk block g's own region
+            const int g = unit / NSEG, seg = unit % NSEG;
+            nf = max(0, min(C.segcap, C.fill[g] - seg * C.segcap));
+            c0 = (int64_t)g * C.cap + (int64_t)seg * C.segcap;
+        } else {
+            // a segment of the shared overflow pool
+            const int64_t v0 = (int64_t)(unit - own_units) * C.segcap;
+            nf = (int)max((int64_t)0, min((int64_t)C.segcap, no_all - v0));
+            c0 = C.ovf_base + v0;
+        }
+        if (nf == 0) continue;
+        s.base[t] = bstart + C.counts[(int64_t)t * C.units + unit];
+        const int nr = (nf + SC_CHUNKS - 1) / SC_CHUNKS;
+        if (t == 0) {
+            issue(c0, nf, 0, 0);
+            if (nr > 1) issue(c0, nf, 1, 1);
+        }
+        __syncthreads();
+        for (int k = 0; k < nr; ++k) {
+            const int b = k & 1;
+            const bool ok = mbar_wait_bounded(&s.bar[b], (phase >> b) & 1u, SC_WAIT_LIMIT);
+            if (ok) {
+                phase ^= 1u << b;
+                in_flight &= ~(1u << b);
+            }
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            process(b, min(SC_CHUNKS, nf - k * SC_CHUNKS));
+            if (t == 0 && k + 2 < nr) issue(c0, nf, k + 2, b);
+        }
+    }
+    if (failed) {
+        if (t == 0) {
+            record_error(ctl, LRCC_ERR_TIMEOUT, -5);
+            // let copies still in flight land before the block's shared memory goes away
+            for (int b = 0; b < 2; ++b)
+                if (in_flight & (1u << b)) mbar_wait_bounded(&s.bar[b], (phase >> b) & 1u, SC_WAIT_LIMIT);
+        }
         __syncthreads();
     }
 }
@@ -897,17 +989,21 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid) {
         // own region per block: its share of the elements in chunks of 8, plus
         // the padding of its share of the sublists, with 30 % slack
         L.cap = (int64_t)(1.1 * (double)n / (double)G / CIDS + 0.6 * (double)L.size[1] / (double)G) + 16;
+        // NSEG segments of an even number of chunks, so every segment's headers
+        // start 16-byte aligned (bulk copies)
+        L.segcap = (int)((L.cap + 2 * NSEG - 1) / (2 * NSEG)) * 2;
+        L.cap = (int64_t)L.segcap * NSEG;
         // the shared pool alone can hold every chunk of a valid list (at most
         // n/8 full chunks plus one partial chunk per sublist), however unevenly
         // the sublists fall on the blocks
         L.ovf_cap = n / CIDS + L.size[1] + 1024;
+        L.ovf_cap += L.ovf_cap & 1;
+        L.units = (int)(G * NSEG + (L.ovf_cap + L.segcap - 1) / L.segcap);
         const int64_t chunks = G * L.cap + L.ovf_cap;
         L.off_ids = take(sizeof(int32_t) * CIDS * (size_t)chunks);
         L.off_meta = take(sizeof(uint64_t) * (size_t)chunks);
-        L.off_ovf_owner = take(sizeof(int32_t) * (size_t)L.ovf_cap);
         L.off_fill = take(sizeof(int) * (size_t)G);
-        L.off_ovf_used = take(sizeof(int) * (size_t)G);
-        L.off_counts = take(sizeof(int) * (size_t)NBK * (size_t)G);
+        L.off_counts = take(sizeof(int) * (size_t)NBK * (size_t)L.units);
         L.off_totals = take(sizeof(int) * (size_t)NBK);
         L.off_vis = take(sizeof(uint32_t) * (size_t)((n + 31) / 32));
     }
@@ -954,13 +1050,13 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     Chunks C;
     C.ids = reinterpret_cast<int32_t*>(base + L.off_ids);
     C.meta = reinterpret_cast<uint64_t*>(base + L.off_meta);
-    C.ovf_owner = reinterpret_cast<int32_t*>(base + L.off_ovf_owner);
     C.fill = reinterpret_cast<int*>(base + L.off_fill);
-    C.ovf_used = reinterpret_cast<int*>(base + L.off_ovf_used);
     C.counts = reinterpret_cast<int*>(base + L.off_counts);
     C.totals = reinterpret_cast<int*>(base + L.off_totals);
     C.vis = reinterpret_cast<uint32_t*>(base + L.off_vis);
     C.cap = L.cap;
+    C.segcap = L.segcap;
+    C.units = L.units;
     C.ovf_cap = L.ovf_cap;
     C.ovf_base = L.grid * L.cap;
     int lg = 0;
@@ -985,6 +1081,8 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     };
     if (L.readonly) {
         cudaMemsetAsync(C.vis, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
+        // overflow units' counts are accumulated with atomics (own units are stored whole)
+        cudaMemsetAsync(C.counts, 0, sizeof(int) * (size_t)NBK * (size_t)L.units, s);
         const int G = (int)L.grid;
         phase_begin(c, s);
         if (p.rs_chains >= 4) rs_walk0c<4><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
@@ -992,7 +1090,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         else rs_walk0c<1><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
         phase_end(c, s, PH_WALK0);
         phase_begin(c, s);
-        rs_scan_counts<<<NBK, SCAN_THREADS, 0, s>>>(C.counts, G, C.totals);
+        rs_scan_counts<<<NBK, SCAN_THREADS, 0, s>>>(C.counts, L.units, C.totals);
         phase_end(c, s, PH_SCAN);
     } else {
         walk(0, W0, n);
@@ -1031,7 +1129,9 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     }
     if (L.readonly) {
         phase_begin(c, s);
-        rs_scatter<<<(int)L.grid, BLOCK, 0, s>>>(C, S(1), W0, n, ctl);
+        cudaFuncSetAttribute((const void*)rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM);
+        const int gs = std::min((int)L.grid, persistent_grid(c, (const void*)rs_scatter, BLOCK, SC_SMEM));
+        rs_scatter<<<gs, BLOCK, SC_SMEM, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
         phase_end(c, s, PH_SCATTER);
         const int g = 2 * c->sms;
         phase_begin(c, s);

@@ -418,6 +418,7 @@ lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out) {
     for (int l = 0; l < c->last_levels && l < 8; ++l) out->splitters[l] = c->last_splitter_cap[l];
     out->rounds = h.rounds;
     out->jump_rounds = h.jump_rounds;
+    out->overflow_chunks = h.ovf_next;
     return LRCC_OK;
 }
 

@@ -160,6 +160,23 @@ def test_stats_report_levels():
     assert st["splitters"] == sorted(st["splitters"], reverse=True)
 
 
+def test_overflow_pool_carries_long_sublists():
+    # read-only first level with few, long sublists: every walk block's own region
+    # (sized for an even share of the elements) overflows into the shared pool,
+    # whose segments the scatter then handles as work units of their own
+    base = lrcc.get_plan(lrcc.KIND_LR, 1 << 18)
+    try:
+        for n, spacing0 in ((1 << 18, 4096), (300_007, 1024), (1 << 18, 64)):
+            lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=2, rs_spacing0=spacing0, rs_small=1024)
+            succ, head = gen.list_random(n, 21)
+            assert np.array_equal(_run("rs", succ, head), oracle.lr_rank(succ, head)), (n, spacing0)
+            if spacing0 >= 1024:
+                assert lrcc.last_stats()["overflow_chunks"] > 0
+    finally:
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_spacing0=base["rs_spacing0"], rs_small=base["rs_small"])
+        _restore_level0()
+
+
 @pytest.mark.slow
 def test_full_size_2p28_random_and_ordered():
     # the bench workload: n = 2^28 in random layout; checked exactly against the

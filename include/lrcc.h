@@ -116,6 +116,27 @@ lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
                      int32_t* label, void* stream);
 
 /*
+ * Host-buffer forms of lr_rank and cc_label: the same arguments and results,
+ * with every array (succ and rank; src, dst and label) in HOST memory. The
+ * call copies the inputs into device staging owned by the stream's context,
+ * runs the device method, and copies the result back, ordered after the
+ * stream's earlier work and before its later work. The copies run on two
+ * copy streams the library keeps per device (uploads, downloads), so calls
+ * queued on different streams pipeline: one call's upload runs at full
+ * bandwidth while another call's kernels run. The call returns once the work
+ * is queued: the output is valid, and the inputs may be changed or freed,
+ * only after `stream` has been synchronised. Not for use inside a stream
+ * capture. Page-locked host buffers (cudaHostAlloc / pinned) make both
+ * copies asynchronous; pageable buffers also work, with copies the driver
+ * stages itself. The staging (8 bytes per list element; 8 bytes per edge plus
+ * 4 per vertex) stays allocated until lrcc_release. Device-detected errors
+ * are reported through lrcc_last_status as for the device forms.
+ */
+lrcc_status lr_rank_host(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
+lrcc_status cc_label_host(const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
+                          int32_t* label, void* stream);
+
+/*
  * Batched list ranking: num_lists independent lists in one launch (a
  * persistent kernel takes the lists from a device work queue, largest first;
  * each list is ranked by one thread block).
@@ -229,7 +250,7 @@ int lrcc_get_l2_fetch_granularity(void);
 /* Frees the workspace and cached graphs of `stream` (waits for it first). */
 lrcc_status lrcc_release(void* stream);
 
-/* Bytes of device workspace currently held by the library (all streams). */
+/* Bytes of device workspace (and host-call staging) currently held by the library (all streams). */
 int64_t lrcc_workspace_bytes(void);
 
 /* Device workspace a call of the given kind and size would need (batched

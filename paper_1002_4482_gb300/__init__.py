@@ -30,6 +30,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIME
 KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
+           "lr_rank_host", "cc_label_host",
            "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "cc_label_batched_sized", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
@@ -77,6 +78,8 @@ def load() -> ctypes.CDLL:
         lib.lr_rank_wyllie.argtypes = [p, i64, i32, p, p]
         lib.lr_rank_noalloc.argtypes = [p, i64, i32, p, p]
         lib.cc_label.argtypes = [p, p, i64, i64, p, p]
+        lib.lr_rank_host.argtypes = [p, i64, i32, p, p]
+        lib.cc_label_host.argtypes = [p, p, i64, i64, p, p]
         lib.lr_rank_batched.argtypes = [p, p, p, i64, p, p]
         lib.lr_rank_batched_sized.argtypes = [p, p, p, i64, i64, p, p]
         lib.cc_label_batched.argtypes = [p, p, p, p, i64, p, p]
@@ -96,7 +99,8 @@ def load() -> ctypes.CDLL:
         lib.lrcc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.lrcc_set_l2_fetch_granularity.argtypes = [i]
         lib.lrcc_get_l2_fetch_granularity.restype = i
-        for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_batched",
+        for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_host", "cc_label_host",
+                  "lr_rank_batched",
                   "lr_rank_batched_sized",
                   "cc_label_batched", "cc_label_batched_sized",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
@@ -136,6 +140,23 @@ def _out(out, n, like, name):
     if out is None:
         return torch.empty(n, dtype=torch.int32, device=like.device)
     _dev_i32(out, name)
+    if out.numel() != n:
+        raise ValueError(f"{name} must hold {n} elements")
+    return out
+
+
+def _host_i32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) int32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _host_out(out, n, name):
+    if out is None:
+        return torch.empty(n, dtype=torch.int32, pin_memory=True)
+    _host_i32(out, name)
     if out.numel() != n:
         raise ValueError(f"{name} must hold {n} elements")
     return out
@@ -184,6 +205,38 @@ def cc_label(src: torch.Tensor, dst: torch.Tensor, n: int, out: torch.Tensor | N
     label = _out(out, n, src, "out")
     _call(load().cc_label(src.data_ptr(), dst.data_ptr(), src.numel(), int(n), label.data_ptr(), _stream(stream)),
           "cc_label")
+    return label
+
+
+def lr_rank_host(succ: torch.Tensor, head: int, out: torch.Tensor | None = None, stream=None,
+                 sync: bool = True) -> torch.Tensor:
+    """:func:`lr_rank` on host tensors: the library copies ``succ`` to the GPU and the ranks back.
+
+    Pinned (page-locked) tensors make the copies asynchronous. With ``sync=False`` the call
+    returns once the work is queued on ``stream``; ``out`` is valid (and ``succ`` may change)
+    only after the stream is synchronised."""
+    _host_i32(succ, "succ")
+    rank = _host_out(out, succ.numel(), "out")
+    s = _stream(stream)
+    _call(load().lr_rank_host(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), s), "lr_rank_host")
+    if sync:
+        (stream or torch.cuda.current_stream()).synchronize()
+    return rank
+
+
+def cc_label_host(src: torch.Tensor, dst: torch.Tensor, n: int, out: torch.Tensor | None = None,
+                  stream=None, sync: bool = True) -> torch.Tensor:
+    """:func:`cc_label` on host tensors (copies in, labels back); ``sync`` as in :func:`lr_rank_host`."""
+    _host_i32(src, "src")
+    _host_i32(dst, "dst")
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst must have the same length")
+    label = _host_out(out, n, "out")
+    s = _stream(stream)
+    _call(load().cc_label_host(src.data_ptr(), dst.data_ptr(), src.numel(), int(n), label.data_ptr(), s),
+          "cc_label_host")
+    if sync:
+        (stream or torch.cuda.current_stream()).synchronize()
     return label
 
 

@@ -76,6 +76,9 @@ struct Ctx {
     DevCtl* ctl = nullptr;            // device control block
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    void* io = nullptr;               // device copies of host-buffer calls' inputs and outputs
+    size_t io_bytes = 0;
+    cudaEvent_t io_ev[4] = {};        // host-buffer calls: staging free, uploaded, computed, downloaded
     int sms = 0;
     std::vector<GraphEntry> graphs;
     uint64_t tick = 0;

@@ -23,6 +23,8 @@ const char* const kPhaseNames[PH_COUNT] = {
     "wy_pack", "wy_jump", "wy_final", "cc_init", "cc_loop", "cc_hook", "cc_shortcut",
     "lr_batch", "cc_batch", "batch_prep", "rs_scan", "rs_scatter"};
 std::map<std::pair<int, cudaStream_t>, Ctx*> g_ctx;
+// per device: the streams that carry the host-buffer calls' uploads and downloads
+std::map<int, std::pair<cudaStream_t, cudaStream_t>> g_copy;
 std::mutex g_plan_mu;
 bool g_plan_init = false;
 Plan g_plan[6][33];
@@ -234,6 +236,71 @@ lrcc_status ensure_ws(Ctx* c, size_t bytes) {
     return LRCC_OK;
 }
 
+// Device staging for the host-buffer entry points (kept apart from the
+// workspace so that its address, and the graphs keyed on it, stay put).
+lrcc_status ensure_io(Ctx* c, size_t bytes) {
+    if (bytes <= c->io_bytes) return LRCC_OK;
+    if (c->io) {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LRCC_ERR_CUDA;
+        drop_graphs(c);
+        cudaFree(c->io);
+        c->io = nullptr;
+        c->io_bytes = 0;
+    }
+    if (cudaMalloc(&c->io, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->io = nullptr;
+        return LRCC_ERR_NOMEM;
+    }
+    c->io_bytes = bytes;
+    return LRCC_OK;
+}
+
+// Runs a host-buffer call: `up` enqueues the uploads, `compute` the device
+// method on the caller's stream, `down` the downloads. Uploads and downloads go
+// through two copy streams shared by all calls on the device, so that the
+// uploads of calls on different streams run one after another at full
+// bandwidth (and overlap other calls' kernels) instead of splitting it.
+// Order: the stream's earlier work (which may still read the staging) ->
+// uploads -> compute -> downloads -> the stream's later work.
+lrcc_status host_call(Ctx* c, const std::function<cudaError_t(cudaStream_t)>& up,
+                      const std::function<lrcc_status()>& compute,
+                      const std::function<cudaError_t(cudaStream_t)>& down) {
+    cudaStream_t in = nullptr, out = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_copy.find(c->device);
+        if (it == g_copy.end()) {
+            if (cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking) != cudaSuccess) return LRCC_ERR_CUDA;
+            if (cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaStreamDestroy(in);
+                return LRCC_ERR_CUDA;
+            }
+            g_copy[c->device] = std::make_pair(in, out);
+        } else {
+            in = it->second.first;
+            out = it->second.second;
+        }
+    }
+    for (auto& e : c->io_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
+            return LRCC_ERR_CUDA;
+        }
+    cudaEvent_t free_ev = c->io_ev[0], in_ev = c->io_ev[1], done_ev = c->io_ev[2], out_ev = c->io_ev[3];
+    if (cudaEventRecord(free_ev, c->stream) != cudaSuccess || cudaStreamWaitEvent(in, free_ev, 0) != cudaSuccess ||
+        up(in) != cudaSuccess || cudaEventRecord(in_ev, in) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stream, in_ev, 0) != cudaSuccess)
+        return LRCC_ERR_CUDA;
+    const lrcc_status st = compute();
+    if (st != LRCC_OK) return st;
+    if (cudaEventRecord(done_ev, c->stream) != cudaSuccess || cudaStreamWaitEvent(out, done_ev, 0) != cudaSuccess ||
+        down(out) != cudaSuccess || cudaEventRecord(out_ev, out) != cudaSuccess ||
+        cudaStreamWaitEvent(c->stream, out_ev, 0) != cudaSuccess)
+        return LRCC_ERR_CUDA;
+    return LRCC_OK;
+}
+
 }  // namespace lrcc
 
 using namespace lrcc;
@@ -255,14 +322,11 @@ const char* lrcc_status_str(int status) {
 
 int lrcc_version(void) { return 100; }
 
-lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
-    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
-    if (n == 0) return LRCC_OK;
-    if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
-    Ctx* c = nullptr;
-    lrcc_status st = ctx_for(stream, &c);
-    if (st != LRCC_OK) return st;
-    std::lock_guard<std::mutex> lk(c->mu);
+namespace {
+
+// lr_rank on device buffers, with the context's lock held.
+lrcc_status lr_rank_locked(Ctx* c, const int32_t* succ, int64_t n, int32_t head, int32_t* rank) {
+    lrcc_status st = LRCC_OK;
     const Plan p = plan_for(KIND_LR, n);
     const RsLayout L = rs_layout(n, p, rs_walk_grid(c, p));
     if (n > p.rs_small) {
@@ -280,6 +344,51 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
     c->last_levels = n > p.rs_small ? L.levels : 0;
     for (int l = 0; l < MAX_LEVELS; ++l) c->last_splitter_cap[l] = l < L.levels ? L.size[l + 1] : 0;
     return st;
+}
+
+// cc_label on device buffers, with the context's lock held.
+lrcc_status cc_label_locked(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label) {
+    const Plan p = plan_for(KIND_CC, n);
+    lrcc_status st = ensure_ws(c, cc_ws(m));
+    if (st != LRCC_OK) return st;
+    reset_ctl(c, c->stream);
+    st = cc_run(c, src, dst, m, n, label, p);
+    c->last_kind = KIND_CC;
+    return st;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return lr_rank_locked(c, succ, n, head, rank);
+}
+
+lrcc_status lr_rank_host(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const size_t bytes = sizeof(int32_t) * (size_t)n;
+    st = ensure_io(c, 2 * align256(bytes));
+    if (st != LRCC_OK) return st;
+    int32_t* d_succ = static_cast<int32_t*>(c->io);
+    int32_t* d_rank = reinterpret_cast<int32_t*>(static_cast<char*>(c->io) + align256(bytes));
+    return host_call(
+        c, [&](cudaStream_t s) { return cudaMemcpyAsync(d_succ, succ, bytes, cudaMemcpyHostToDevice, s); },
+        [&] { return lr_rank_locked(c, d_succ, n, head, d_rank); },
+        [&](cudaStream_t s) { return cudaMemcpyAsync(rank, d_rank, bytes, cudaMemcpyDeviceToHost, s); });
 }
 
 lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
@@ -315,13 +424,34 @@ lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
     lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
-    const Plan p = plan_for(KIND_CC, n);
-    st = ensure_ws(c, cc_ws(m));
+    return cc_label_locked(c, src, dst, m, n, label);
+}
+
+lrcc_status cc_label_host(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label,
+                          void* stream) {
+    if (n < 0 || m < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return m == 0 ? LRCC_OK : LRCC_ERR_ARG;
+    if (!label || (m > 0 && (!src || !dst))) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;
-    reset_ctl(c, c->stream);
-    st = cc_run(c, src, dst, m, n, label, p);
-    c->last_kind = KIND_CC;
-    return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const size_t eb = sizeof(int32_t) * (size_t)m, vb = sizeof(int32_t) * (size_t)n;
+    st = ensure_io(c, 2 * align256(eb) + align256(vb));
+    if (st != LRCC_OK) return st;
+    char* io = static_cast<char*>(c->io);
+    int32_t* d_src = reinterpret_cast<int32_t*>(io);
+    int32_t* d_dst = reinterpret_cast<int32_t*>(io + align256(eb));
+    int32_t* d_label = reinterpret_cast<int32_t*>(io + 2 * align256(eb));
+    return host_call(
+        c,
+        [&](cudaStream_t s) {
+            if (m == 0) return cudaSuccess;
+            const cudaError_t e = cudaMemcpyAsync(d_src, src, eb, cudaMemcpyHostToDevice, s);
+            return e != cudaSuccess ? e : cudaMemcpyAsync(d_dst, dst, eb, cudaMemcpyHostToDevice, s);
+        },
+        [&] { return cc_label_locked(c, d_src, d_dst, m, n, d_label); },
+        [&](cudaStream_t s) { return cudaMemcpyAsync(label, d_label, vb, cudaMemcpyDeviceToHost, s); });
 }
 
 lrcc_status lr_rank_batched_sized(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
@@ -525,6 +655,9 @@ lrcc_status lrcc_release(void* stream) {
     drop_graphs(c);
     for (auto e : c->events) cudaEventDestroy(e);
     if (c->ws) cudaFree(c->ws);
+    if (c->io) cudaFree(c->io);
+    for (auto e : c->io_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(c->ctl);
     cudaStreamDestroy(c->capture);
     delete c;
@@ -534,7 +667,7 @@ lrcc_status lrcc_release(void* stream) {
 int64_t lrcc_workspace_bytes(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     int64_t t = 0;
-    for (auto& kv : g_ctx) t += (int64_t)kv.second->ws_bytes + (int64_t)sizeof(DevCtl);
+    for (auto& kv : g_ctx) t += (int64_t)(kv.second->ws_bytes + kv.second->io_bytes) + (int64_t)sizeof(DevCtl);
     return t;
 }
 

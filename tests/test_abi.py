@@ -44,6 +44,27 @@ def test_binding_names_match_header():
     assert set(lrcc.SYMBOLS) == set(declared_functions())
 
 
+def declared_arity():
+    """Parameter count of every function prototype in the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(([^()]*)\)\s*;", text):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_declares_argument_types_for_every_call():
+    # a ctypes call without argtypes passes Python ints as 32-bit C ints, which
+    # truncates 64-bit pointers and sizes: every function with parameters needs them
+    L = lrcc.load()
+    for name, k in declared_arity().items():
+        if k == 0:
+            continue
+        at = getattr(L, name).argtypes
+        assert at is not None and len(at) == k, f"{name}: argtypes {at} for {k} parameters"
+
+
 def test_status_strings(lib):
     lrcc.load()
     assert lrcc.status_str(0) == "ok"

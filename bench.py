@@ -35,7 +35,7 @@ UNIT = "M(list nodes + graph edges)/s"
 
 # ncu DRAM bytes of one first-level walk launch (rs_walk0c) at n = 2^28, random
 # layout: dram__bytes_read.sum + dram__bytes_write.sum of a capture at n = 2^26
-# (7.582 GB + 0.420 GB, profiles/rs_walk0c_lr2p26.md) scaled by the 4x elements,
+# (7.582 GB + 0.420 GB; ncu of `profile_case lr 26 readonly`) scaled by the 4x elements,
 # and the hash of lr.cu it was taken from. Reported only while lr.cu is unchanged.
 NCU_WALK0 = {"lr_cu_sha1": "77d4fc5f9eb4ea33037947186f87ca3a9744dd96", "bytes_per_launch": 4 * (7.581555e9 + 0.420289e9)}
 

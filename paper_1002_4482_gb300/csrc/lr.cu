@@ -530,7 +530,7 @@ struct ScatterSmem {
     uint16_t tile[SC_ITEMS];       // slot indices sorted by bucket
     int cnt[2][NBK];               // elements per bucket in the round (alternating)
     int base[NBK];                 // next free pair of each bucket for this region
-    int start[NBK];                // global start of each bucket's run in the round
+    int delta[NBK];                // pair position minus tile slot, per bucket, in the round
     int tstart[NBK];               // start of each bucket's run in the tile
     int warp[BLOCK / 32];
     uint64_t bar[2];
@@ -614,7 +614,9 @@ __global__ void __launch_bounds__(BLOCK, 4)
     // first id is -1 is empty)
     auto process = [&](int b, int cnt) {
         int* cntp = s.cnt[par];
-        // the owners' suffix ranks first (L2 gathers), so their latency overlaps the counting
+        // the owners' suffix ranks (L2 gathers) are issued first and stored to shared
+        // memory only after the tile is built, so their latency overlaps the counting,
+        // the scan and the tile
         int32_t top[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -632,15 +634,13 @@ __global__ void __launch_bounds__(BLOCK, 4)
             for (int q = 0; q < CIDS; ++q)
                 loc[u][q] = (c < cnt && id[q] >= 0) ? atomicAdd(&cntp[id[q] >> C.shift], 1) : 0;
         }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) s.top[u * BLOCK + t] = top[u];
         __syncthreads();
         const int h = s.cnt[par][t];
         s.cnt[par ^ 1][t] = 0;      // counts of the next round
         int items = 0;
         const int ts = block_scan(h, &items);
         s.tstart[t] = ts;
-        s.start[t] = s.base[t];
+        s.delta[t] = s.base[t] - ts;   // pair position of tile slot i of bucket t: delta[t] + i
         s.base[t] += h;
         __syncthreads();
 #pragma unroll
@@ -652,12 +652,13 @@ __global__ void __launch_bounds__(BLOCK, 4)
             for (int q = 0; q < CIDS; ++q)
                 if (c < cnt && id[q] >= 0) s.tile[s.tstart[id[q] >> C.shift] + loc[u][q]] = (uint16_t)(c * CIDS + q);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) s.top[u * BLOCK + t] = top[u];
         __syncthreads();
         for (int i = t; i < items; i += BLOCK) {
             const int x = s.tile[i];
             const int32_t id = s.ids[b][x];
-            const int bk = id >> C.shift;
-            const int64_t pos = (int64_t)s.start[bk] + (i - s.tstart[bk]);
+            const int64_t pos = (int64_t)s.delta[id >> C.shift] + i;
             if (pos < n) pairs[pos] = pack((uint32_t)id, (uint32_t)(s.top[x >> 3] - (x & 7)));
         }
         fence_proxy_async_smem();   // the buffer's reads come before the next bulk copy into it

@@ -213,6 +213,11 @@ typedef struct lrcc_plan {
                                 as 32-byte chunks, which are turned into ranks by a scatter
                                 into id-range buckets and a placement pass */
     uint64_t seed;           /* splitter seed (results do not depend on it) */
+    int32_t cc_sample;       /* components: before the first pass over all edges, one hook pass
+                                and shortcut over the first m / cc_sample edges (a sample that
+                                forms most of the large components cheaply); 1 = no sample pass,
+                                -1 = automatic (about 4 sampled edges per vertex, on graphs with
+                                at least 8 edges per vertex) */
 } lrcc_plan;
 
 /* kind: 1 = list ranking, 3 = connected components; sizes with ceil(log2 n)

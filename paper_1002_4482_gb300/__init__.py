@@ -54,7 +54,7 @@ class Plan(ctypes.Structure):
                 ("rs_small", ctypes.c_int32), ("rs_chains", ctypes.c_int32),
                 ("cc_hook", ctypes.c_int32), ("cc_max_rounds", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("rs_level0", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("cc_sample", ctypes.c_int32)]
 
 
 def library_path() -> str:

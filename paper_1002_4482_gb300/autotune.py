@@ -9,7 +9,7 @@ the min-id invariants), so a wrong plan can never win.
 Knobs searched:
   lists       first-level mode (in-place words / read-only walk), spacing at the
               first and deeper levels, walks per thread, one-block cutoff
-  components  hook rule (single hook / re-link / single then re-link)
+  components  hook rule (single hook / re-link / single then re-link), sample pass size
   batched     minimum splitter spacing of in-block ruling sets; hook rule of the
               large-graph union path
 
@@ -116,8 +116,8 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print):
                 cases.append((torch.from_numpy(s_).to(dev), torch.from_numpy(d_).to(dev), n_,
                               torch.empty(n_, dtype=torch.int32, device=dev), s_, d_))
         best = None
-        for hook in (1, 2, 3):
-            set_plan(KIND_CC, c, c, cc_hook=hook)
+        for hook, samp in itertools.product((1, 2, 3), (-1, 1, 4, 8)):
+            set_plan(KIND_CC, c, c, cc_hook=hook, cc_sample=samp)
             ms = 0.0
             for sd, dd, n_, lab, s_np, d_np in cases:
                 ms += _timeit(lambda: cc_label(sd, dd, n_, out=lab, stream=stream), stream)
@@ -126,9 +126,9 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print):
                         bool((lab <= torch.arange(n_, device=dev, dtype=torch.int32)).all()) and \
                         bool(torch.equal(lab[lab.long()], lab))
                 if not ok:
-                    raise AssertionError(f"hook rule {hook} broke the label invariants at 2^{c}")
+                    raise AssertionError(f"hook rule {hook}, sample {samp} broke the label invariants at 2^{c}")
             if best is None or ms < best[0]:
-                best = (ms, {"cc_hook": hook})
+                best = (ms, {"cc_hook": hook, "cc_sample": samp})
         set_plan(KIND_CC, lo, hi, **best[1])
         results[str(c)] = {"range": [lo, hi], "ms": best[0], "plan": best[1]}
         log(f"graphs 2^{c}: {best[0]:.3f} ms with {best[1]}")

@@ -242,6 +242,15 @@ __global__ void cc_control_host(DevCtl* ctl, int cap, bool compacting) {
     ctl->pad[0] = cont;
 }
 
+// After the sample pass: it counts as the first round (parents are no longer
+// the vertices themselves, so the next pass, over all edges, compacts), and
+// its change flag is dropped (the loop's own passes decide convergence).
+__global__ void cc_sample_done(DevCtl* ctl) {
+    ctl->rounds = 1;
+    ctl->flag = 0;
+    ctl->cc_stop = 0;
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 struct CcArgs {
@@ -353,6 +362,30 @@ lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, in
     if (aligned16(label)) cc_init<true><<<gi, BLOCK, 0, s>>>(label, n);
     else cc_init<false><<<gi, BLOCK, 0, s>>>(label, n);
     phase_end(c, s, PH_CC_INIT);
+
+    // Sample pass: hook and shortcut over a prefix of the edge list first. On
+    // graphs with large components this forms most of them for a fraction of a
+    // pass, and the first pass over all edges then finds most edges inside one
+    // tree and drops them. Which edges are hooked first does not change the
+    // labels; the loop below still runs until a pass over the remaining edges
+    // joins nothing.
+    int samp = p.cc_sample;
+    if (samp < 0) {
+        // automatic: about 4 sampled edges per vertex, when there are at least 8
+        const int64_t per_vertex = n > 0 ? m / n : 0;
+        samp = per_vertex >= 8 ? (int)std::min<int64_t>(per_vertex / 4, 1024) : 1;
+    }
+    const int64_t ms = samp > 1 ? m / samp : 0;
+    if (ms >= 4096 && a.act.cap > 0) {
+        CcArgs sa = a;
+        sa.m = ms;
+        sa.act = ActiveEdges{};
+        lrcc_status st = enqueue_hook(c, s, sa);
+        if (st != LRCC_OK) return st;
+        cc_sample_done<<<1, 1, 0, s>>>(c->ctl);
+        st = enqueue_shortcut(c, s, sa);
+        if (st != LRCC_OK) return st;
+    }
 
     if (p.use_graphs != 2) {
         const std::vector<uint64_t> key = {(uint64_t)KIND_CC, (uint64_t)src, (uint64_t)dst, (uint64_t)m,

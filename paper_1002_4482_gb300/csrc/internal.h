@@ -31,6 +31,7 @@ struct Plan {
     int cc_hook = 1;
     int cc_max_rounds = 0;
     int use_graphs = 1;
+    int cc_sample = -1;     // 1 = no sample pass; k = a first pass over the first m / k edges; -1 = auto
     uint64_t seed = 0x5eedULL;
 };
 Plan plan_for(int kind, int64_t n);

@@ -110,7 +110,8 @@ lrcc_status launch_recorded(Ctx* c, const Plan& p, std::vector<uint64_t> key,
 
 std::vector<uint64_t> plan_key(const Plan& p) {
     return {(uint64_t)p.rs_spacing0, (uint64_t)p.rs_spacing, (uint64_t)p.rs_small, (uint64_t)p.rs_chains,
-            (uint64_t)p.rs_level0, (uint64_t)p.cc_hook, (uint64_t)p.cc_max_rounds, p.seed};
+            (uint64_t)p.rs_level0, (uint64_t)p.cc_hook, (uint64_t)p.cc_max_rounds, p.seed,
+            (uint64_t)p.cc_sample};
 }
 
 }  // namespace
@@ -558,7 +559,8 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
         (plan->rs_spacing0 > 0 && plan->rs_spacing0 < 2) || (plan->rs_spacing > 0 && plan->rs_spacing < 2) ||
         (plan->rs_small > 0 && plan->rs_small < 1024) || plan->rs_chains < 0 || plan->rs_chains > 4 ||
         plan->cc_hook < 0 || plan->cc_hook > 3 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
-        plan->use_graphs > 2 || plan->rs_level0 < 0 || plan->rs_level0 > 2)
+        plan->use_graphs > 2 || plan->rs_level0 < 0 || plan->rs_level0 > 2 || plan->cc_sample < -1 ||
+        plan->cc_sample > 1024)
         return LRCC_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_plan_mu);
     init_plans_locked();
@@ -573,6 +575,7 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
         if (plan->use_graphs) p.use_graphs = plan->use_graphs;
         if (plan->rs_level0) p.rs_level0 = plan->rs_level0;
         if (plan->seed) p.seed = plan->seed;
+        if (plan->cc_sample) p.cc_sample = plan->cc_sample;
     }
     return LRCC_OK;
 }
@@ -590,6 +593,7 @@ lrcc_status lrcc_get_plan(int kind, int64_t n, lrcc_plan* out) {
     out->use_graphs = p.use_graphs;
     out->rs_level0 = p.rs_level0;
     out->seed = p.seed;
+    out->cc_sample = p.cc_sample;
     return LRCC_OK;
 }
 

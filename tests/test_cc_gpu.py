@@ -126,6 +126,33 @@ def test_round_cap_is_reported():
     assert np.array_equal(_run(src, dst, 5000), oracle.cc_uf(src, dst, 5000))
 
 
+@pytest.mark.parametrize("sample", [1, 2, 8, 64, -1], ids=["off", "half", "eighth", "1/64", "auto"])
+def test_sample_pass_keeps_labels(hook, sample):
+    # the sample pass hooks a prefix of the edge list first; labels must not change,
+    # whatever the prefix holds: dense random graphs, many small components, a
+    # prefix that already holds every edge (the list repeated), and a long path
+    # whose prefix is one piece of it
+    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 16)["cc_sample"]
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=sample)
+    try:
+        src, dst = gen.er(1 << 16, 1 << 20, 41)           # 16 edges per vertex
+        assert np.array_equal(_run(src, dst, 1 << 16), oracle.cc_uf(src, dst, 1 << 16))
+        src, dst = gen.er(1 << 17, 1 << 17, 42)           # one edge per vertex: small components
+        assert np.array_equal(_run(src, dst, 1 << 17), oracle.cc_uf(src, dst, 1 << 17))
+        s1, d1 = gen.er(50_000, 20_000, 43)
+        src, dst = np.tile(s1, 8), np.tile(d1, 8)          # the prefix is the whole edge set
+        assert np.array_equal(_run(src, dst, 50_000), oracle.cc_uf(s1, d1, 50_000))
+        n = 300_000
+        relabel = gen.permutation(n, 44)
+        src = relabel[:-1].astype(np.int32)
+        dst = relabel[1:].astype(np.int32)                 # one path, edges in path order
+        assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
+        src, dst, n = workloads.cc_rmat(16, 16)
+        assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
+    finally:
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=base)
+
+
 @pytest.mark.slow
 def test_full_size_rmat_scale24(hook):
     # the bench workload: R-MAT 2^24 vertices, 2^28 edges, against the union-find oracle

@@ -216,8 +216,8 @@ typedef struct lrcc_plan {
     int32_t cc_sample;       /* components: before the first pass over all edges, one hook pass
                                 and shortcut over the first m / cc_sample edges (a sample that
                                 forms most of the large components cheaply); 1 = no sample pass,
-                                -1 = automatic (about 4 sampled edges per vertex, on graphs with
-                                at least 8 edges per vertex) */
+                                -1 = automatic (about one sampled edge per vertex on graphs with
+                                at least 8 edges per vertex, two with 4 to 7, no sample below) */
 } lrcc_plan;
 
 /* kind: 1 = list ranking, 3 = connected components; sizes with ceil(log2 n)

@@ -436,6 +436,7 @@ struct SegActive {
 // entries stay in L2 (a grid-stride loop would let blocks drift across many
 // graphs, whose parent arrays together are far larger than L2).
 constexpr int SEG_SLICE = SEG_BLOCK * 64;
+constexpr int SEG_STAGE = 32 * SEG_RUN;   // active edges a warp stages before appending
 
 __global__ void __launch_bounds__(SEG_BLOCK)
     seg_hook(LargeSet L, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
@@ -452,6 +453,23 @@ __global__ void __launch_bounds__(SEG_BLOCK)
     const int64_t E = sel == 0 ? L.lep[nl] : min((int64_t)ctl->cc_count[sel], act.cap);
     const int lane = threadIdx.x & 31;
     bool changed = false;
+    // active edges are staged per warp and appended in batches (one counter
+    // atomic per batch instead of one per warp iteration)
+    __shared__ int2 s_stage[SEG_BLOCK / 32][SEG_STAGE];
+    int2* stage = s_stage[threadIdx.x >> 5];
+    int2* out = act.buf[out_sel - 1];
+    int staged = 0;   // warp-uniform
+    auto flush = [&]() {
+        __syncwarp();
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->cc_count[out_sel], staged);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane == 0 && (int64_t)base + staged > act.cap) ctl->cc_overflow = 1;
+        for (int j = lane; j < staged; j += 32)
+            if ((int64_t)base + j < act.cap) out[base + j] = stage[j];
+        __syncwarp();
+        staged = 0;
+    };
     for (;;) {
         if (threadIdx.x == 0) s_slice = atomicAdd(&ctl->seg_next, 1);
         __syncthreads();
@@ -508,21 +526,16 @@ __global__ void __launch_bounds__(SEG_BLOCK)
                     if (lane >= o) incl += t;
                 }
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
-                int base = 0;
-                if (lane == 31 && total) base = atomicAdd(&ctl->cc_count[out_sel], total);
-                base = __shfl_sync(0xffffffffu, base, 31);
-                if (lane == 31 && total && (int64_t)base + total > act.cap) ctl->cc_overflow = 1;
-                int64_t at = (int64_t)base + incl - nkeep;
-                int2* out = act.buf[out_sel - 1];
+                if (staged + total > SEG_STAGE) flush();
+                int at = staged + incl - nkeep;
 #pragma unroll
                 for (int q = 0; q < SEG_RUN; ++q)
-                    if (u[q] >= 0) {
-                        if (at < act.cap) out[at] = make_int2(u[q], v[q]);
-                        ++at;
-                    }
+                    if (u[q] >= 0) stage[at++] = make_int2(u[q], v[q]);
+                staged += total;
             }
         }
     }
+    if (compact && staged > 0) flush();
     if (__any_sync(0xffffffffu, changed) && lane == 0) ctl->flag = 1;
 }
 

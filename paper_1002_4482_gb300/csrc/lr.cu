@@ -512,20 +512,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int 
 
 // Chunks of walk block g -> (element, rank) pairs at block g's offsets of
 // each bucket. Radix-partition style, in rounds of SC_CHUNKS chunks: the
-// round's chunk ids and headers arrive in shared memory by bulk copy (two
-// buffers, the next round in flight while this one is processed), the
+// round's chunk ids and headers arrive in shared memory by bulk copy (SC_BUF
+// buffers: the next rounds in flight while this one is processed), the
 // round's elements are ranked by bucket with shared atomics, their indices
 // laid out sorted by bucket in a tile, and every bucket's run is written
 // with coalesced stores at the block's next offset for that bucket. Blocks
 // are persistent and take work units u = blockIdx.x, + gridDim.x, ...: the
 // NSEG segments of every walk block's region, then the segments of the shared
 // overflow pool (each unit's per-bucket counts come from the walk).
-constexpr int SC_CHUNKS = 2 * BLOCK;            // chunks per round, two per thread
+constexpr int SC_U = 2;                         // chunks per thread and round
+constexpr int SC_BUF = 2;                       // rounds staged in shared memory (in flight + current)
+constexpr int SC_CHUNKS = SC_U * BLOCK;         // chunks per round
 constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
 constexpr int SC_WAIT_LIMIT = 1 << 22;          // polls of a bulk-copy barrier before giving up
 struct ScatterSmem {
-    int32_t ids[2][SC_ITEMS];      // chunk ids of the round in each buffer
-    uint64_t meta[2][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
+    int32_t ids[SC_BUF][SC_ITEMS];      // chunk ids of the round in each buffer
+    uint64_t meta[SC_BUF][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
     int32_t top[SC_CHUNKS];        // rank of the first element of each chunk
     uint16_t tile[SC_ITEMS];       // slot indices sorted by bucket
     int cnt[2][NBK];               // elements per bucket in the round (alternating)
@@ -533,7 +535,7 @@ struct ScatterSmem {
     int delta[NBK];                // pair position minus tile slot, per bucket, in the round
     int tstart[NBK];               // start of each bucket's run in the tile
     int warp[BLOCK / 32];
-    uint64_t bar[2];
+    uint64_t bar[SC_BUF];
 };
 constexpr size_t SC_SMEM = sizeof(ScatterSmem);
 
@@ -586,8 +588,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
     }
     s.cnt[0][t] = s.cnt[1][t] = 0;
     if (t == 0) {
-        mbar_init(&s.bar[0], 1);
-        mbar_init(&s.bar[1], 1);
+        for (int b = 0; b < SC_BUF; ++b) mbar_init(&s.bar[b], 1);
         fence_proxy_async_smem();   // the initialised barriers are visible to the bulk copies
     }
     __syncthreads();
@@ -617,16 +618,16 @@ __global__ void __launch_bounds__(BLOCK, 4)
         // the owners' suffix ranks (L2 gathers) are issued first and stored to shared
         // memory only after the tile is built, so their latency overlaps the counting,
         // the scan and the tile
-        int32_t top[2];
+        int32_t top[SC_U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < SC_U; ++u) {
             const int c = u * BLOCK + t;
             const uint64_t mt = s.meta[b][c];
             top[u] = (c < cnt && s.ids[b][c * CIDS] >= 0) ? __ldg(S1 + lo32(mt)) - 1 - (int32_t)hi32(mt) : 0;
         }
-        int loc[2][CIDS];
+        int loc[SC_U][CIDS];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < SC_U; ++u) {
             const int c = u * BLOCK + t;
             int32_t id[CIDS];
             load_chunk(&s.ids[b][c * CIDS], id);
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
         s.base[t] += h;
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < SC_U; ++u) {
             const int c = u * BLOCK + t;
             int32_t id[CIDS];
             load_chunk(&s.ids[b][c * CIDS], id);
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
                 if (c < cnt && id[q] >= 0) s.tile[s.tstart[id[q] >> C.shift] + loc[u][q]] = (uint16_t)(c * CIDS + q);
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) s.top[u * BLOCK + t] = top[u];
+        for (int u = 0; u < SC_U; ++u) s.top[u * BLOCK + t] = top[u];
         __syncthreads();
         for (int i = t; i < items; i += BLOCK) {
             const int x = s.tile[i];
@@ -685,13 +686,11 @@ __global__ void __launch_bounds__(BLOCK, 4)
         if (nf == 0) continue;
         s.base[t] = bstart + C.counts[(int64_t)t * C.units + unit];
         const int nr = (nf + SC_CHUNKS - 1) / SC_CHUNKS;
-        if (t == 0) {
-            issue(c0, nf, 0, 0);
-            if (nr > 1) issue(c0, nf, 1, 1);
-        }
+        if (t == 0)
+            for (int k = 0; k < SC_BUF && k < nr; ++k) issue(c0, nf, k, k);
         __syncthreads();
         for (int k = 0; k < nr; ++k) {
-            const int b = k & 1;
+            const int b = k % SC_BUF;
             const bool ok = mbar_wait_bounded(&s.bar[b], (phase >> b) & 1u, SC_WAIT_LIMIT);
             if (ok) {
                 phase ^= 1u << b;
@@ -702,14 +701,14 @@ __global__ void __launch_bounds__(BLOCK, 4)
                 break;
             }
             process(b, min(SC_CHUNKS, nf - k * SC_CHUNKS));
-            if (t == 0 && k + 2 < nr) issue(c0, nf, k + 2, b);
+            if (t == 0 && k + SC_BUF < nr) issue(c0, nf, k + SC_BUF, b);
         }
     }
     if (failed) {
         if (t == 0) {
             record_error(ctl, LRCC_ERR_TIMEOUT, -5);
             // let copies still in flight land before the block's shared memory goes away
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < SC_BUF; ++b)
                 if (in_flight & (1u << b)) mbar_wait_bounded(&s.bar[b], (phase >> b) & 1u, SC_WAIT_LIMIT);
         }
         __syncthreads();

@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -54,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-families", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=400)
     ap.add_argument("--plain-launches", action="store_true",
@@ -227,6 +229,55 @@ def random_gather_peak(torch, dev, stream, log2n=28):
     del a, idx, out
     torch.cuda.empty_cache()
     return (1 << log2n) / (ms / 1e3) / 1e9
+
+
+def bench_families(lrcc, torch, dev, stream, m=8_000_000):
+    """The paper's component families (Sec. 4): collections of random lists, random
+    trees of degree k and random graphs of edge density d, all with m edges; hook
+    passes and time of the default rule (atomicMin hooking with the sample pass)
+    against the Shiloach-Vishkin rounds (hook rule 4)."""
+    import gen
+    out = []
+    cases = [("lists", 1, None)] + [("trees", k, None) for k in (2, 3, 5, 10, 20)] + \
+            [("random", None, d) for d in (0.001, 0.01)]
+    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 20)
+    for kind, k, d in cases:
+        if kind == "lists":
+            src, dst, n = gen.list_graph(8, m // 8 + 1, 61)
+        elif kind == "trees":
+            src, dst, n = gen.tree_graph(8, m // 8 + 1, k, 62)
+        else:
+            n = gen.density_vertices(m, d)
+            src, dst = gen.er(n, m, 63)
+        with torch.cuda.stream(stream):
+            S = torch.from_numpy(src).to(dev)
+            D = torch.from_numpy(dst).to(dev)
+            lab = torch.empty(n, dtype=torch.int32, device=dev)
+        row = {"family": kind, "k": k, "density": d, "n": n, "m": len(src)}
+        ref = None
+        for name, hook in (("atomicmin", base["cc_hook"]), ("shiloach_vishkin", 4)):
+            lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=hook)
+            lrcc.cc_label(S, D, n, out=lab, stream=stream)
+            stream.synchronize()
+            best = float("inf")
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lrcc.cc_label(S, D, n, out=lab, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                best = min(best, a.elapsed_time(b))
+            lrcc.check(stream)
+            row[name] = {"ms": best, "rounds": lrcc.last_stats(stream)["rounds"]}
+            if ref is None:
+                ref = lab.clone()
+            elif not torch.equal(ref, lab):
+                raise AssertionError(f"hook rules disagree on {kind} {k} {d}")
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=base["cc_hook"])
+        row["sv_round_bound"] = int(math.floor(math.log(n) / math.log(1.5))) + 2
+        out.append(row)
+        del S, D, lab, ref
+    return out
 
 
 def bench_batched(lrcc, torch, dev, stream, log2_count=12):
@@ -571,6 +622,9 @@ def main():
                "host_cores": os.cpu_count()}
 
     batched = serving = None
+    families = None
+    if rank == 0 and not args.no_families:
+        families = bench_families(lrcc, torch, dev, stream)
     if rank == 0 and not args.no_batched:
         del rank_out, label, src, dst, succ
         torch.cuda.empty_cache()
@@ -599,7 +653,7 @@ def main():
                        "problem_bytes_frac": (8 * m_cc + 4 * n_cc) / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
                        "rounds": cc_stats["rounds"]},
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
-                "batched": batched, "serving": serving,
+                "batched": batched, "serving": serving, "cc_families": families,
                 **extra}
         print(json.dumps(line), flush=True)
     if world > 1:

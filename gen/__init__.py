@@ -57,6 +57,10 @@ def _load():
             lib.gen_list_batch.restype = ctypes.c_int
             lib.gen_er_batch.argtypes = [i64, p, i64, i64, u64, p, p, p, p]
             lib.gen_jobs.argtypes = [i64, dbl, dbl, dbl, dbl, u64, p, p, p]
+            lib.gen_list_graph.argtypes = [i64, i64, u64, p, p]
+            lib.gen_list_graph.restype = ctypes.c_int
+            lib.gen_tree_graph.argtypes = [i64, i64, i64, u64, p, p]
+            lib.gen_tree_graph.restype = ctypes.c_int
             lib.gen_splitmix64_at.argtypes = [u64, u64]
             lib.gen_splitmix64_at.restype = u64
             _lib = lib
@@ -109,6 +113,33 @@ def rmat(scale: int, m: int, a: float, b: float, c: float, seed: int):
     if lib.gen_rmat(scale, m, a, b, c, seed, _ptr(src), _ptr(dst)):
         raise ValueError("gen_rmat failed")
     return src, dst
+
+
+def list_graph(count: int, size: int, seed: int):
+    """count paths of `size` vertices at random ids: (src, dst, n)."""
+    lib = _load()
+    m = count * max(size - 1, 0)
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    if lib.gen_list_graph(count, size, seed, _ptr(src), _ptr(dst)):
+        raise MemoryError("gen_list_graph failed")
+    return src, dst, count * size
+
+
+def tree_graph(count: int, size: int, k: int, seed: int):
+    """count random trees of `size` vertices, at most k children each: (src, dst, n)."""
+    lib = _load()
+    m = count * max(size - 1, 0)
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    if lib.gen_tree_graph(count, size, k, seed, _ptr(src), _ptr(dst)):
+        raise MemoryError("gen_tree_graph failed")
+    return src, dst, count * size
+
+
+def density_vertices(m: int, d: float) -> int:
+    """Vertex count n of a graph with m edges and edge density d = m / (n (n - 1) / 2)."""
+    return int(round((1.0 + (1.0 + 8.0 * m / d) ** 0.5) / 2.0))
 
 
 def loguniform_sizes(count: int, lo: float, hi: float, seed: int) -> np.ndarray:

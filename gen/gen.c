@@ -219,5 +219,64 @@ void gen_jobs(int64_t count, double mean_gap, double p_list, double lo, double h
     }
 }
 
+/*
+ * The graph families of the paper's component experiments (Sec. 4: list
+ * graphs, trees of degree k, random graphs of edge density d), as read here.
+ * Vertex ids are a random permutation of [0, count*size), so each structure
+ * sits at random places of the id space.
+ *
+ * List graph: count paths of `size` vertices; edge (perm[c*size+i],
+ * perm[c*size+i+1]) joins consecutive vertices of path c.
+ * m = count * (size - 1).
+ */
+int gen_list_graph(int64_t count, int64_t size, uint64_t seed, int32_t* src, int32_t* dst) {
+    const int64_t n = count * size;
+    int32_t* perm = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!perm) return 2;
+    gen_permutation(n, derive(seed, 11), perm);
+    int64_t e = 0;
+    for (int64_t c = 0; c < count; ++c)
+        for (int64_t i = 0; i + 1 < size; ++i, ++e) {
+            src[e] = perm[c * size + i];
+            dst[e] = perm[c * size + i + 1];
+        }
+    free(perm);
+    return 0;
+}
+
+/*
+ * Tree graph: count random trees of `size` vertices and degree k (at most k
+ * children per vertex). Each tree grows one vertex at a time: vertex t takes
+ * a child slot drawn uniformly from the open slots of vertices 0..t-1 (every
+ * vertex brings k slots), the random recursive tree with bounded degree.
+ * Edge (child, parent); m = count * (size - 1).
+ */
+int gen_tree_graph(int64_t count, int64_t size, int64_t k, uint64_t seed, int32_t* src, int32_t* dst) {
+    if (k < 1) return 1;
+    const int64_t n = count * size;
+    int32_t* perm = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* slots = (int32_t*)malloc((size_t)(size * k + 1) * sizeof(int32_t));
+    if (!perm || !slots) { free(perm); free(slots); return 2; }
+    gen_permutation(n, derive(seed, 12), perm);
+    sm64 g = { derive(seed, 13) };
+    int64_t e = 0;
+    for (int64_t c = 0; c < count; ++c) {
+        const int32_t* id = perm + c * size;
+        int64_t open = 0;
+        for (int64_t j = 0; j < k; ++j) slots[open++] = 0;      /* the root's slots */
+        for (int64_t t = 1; t < size; ++t, ++e) {
+            const int64_t r = (int64_t)sm64_bounded(&g, (uint64_t)open);
+            const int32_t parent = slots[r];
+            slots[r] = slots[--open];
+            src[e] = id[t];
+            dst[e] = id[parent];
+            for (int64_t j = 0; j < k; ++j) slots[open++] = (int32_t)t;
+        }
+    }
+    free(perm);
+    free(slots);
+    return 0;
+}
+
 /* Raw access to the stream for tests of the generator itself. */
 uint64_t gen_splitmix64_at(uint64_t seed, uint64_t k) { return sm64_at(seed, k); }

@@ -205,7 +205,10 @@ typedef struct lrcc_plan {
     int32_t rs_small;        /* lists of at most this many elements are ranked by one block */
     int32_t rs_chains;       /* sublist walks interleaved per thread: 1, 2 or 4 */
     int32_t cc_hook;         /* 1 = one atomicMin per edge and pass, 2 = re-link until joined,
-                                3 = rule 1 in the first pass, rule 2 after */
+                                3 = rule 1 in the first pass, rule 2 after, 4 = the
+                                Shiloach-Vishkin rounds themselves (shortcut, mark, conditional
+                                and stagnant-tree hooking, shortcut, check; Sec. 4 SV0-SV5);
+                                same labels; batched calls treat 4 as 1 */
     int32_t cc_max_rounds;   /* cap on hook passes (-1 = back to the automatic cap) */
     int32_t use_graphs;      /* 1 = replay captured CUDA graphs, 2 = plain launches */
     int32_t rs_level0;       /* first ruling-set level: 1 = the walk rewrites 8-byte words in

@@ -122,6 +122,11 @@ lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, in
                    int32_t* label, const Plan& p);
 int64_t cc_active_cap(int64_t m);
 size_t cc_ws(int64_t m);
+// The Shiloach-Vishkin round structure (plan.cc_hook = 4): workspace, run, round bound.
+size_t cc_sv_ws(int64_t n);
+lrcc_status cc_run_sv(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label,
+                      const Plan& p);
+int sv_round_bound(int64_t n);
 
 // --- batched (batch.cu)
 lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, const int32_t* heads,

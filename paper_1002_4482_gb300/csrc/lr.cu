@@ -742,14 +742,16 @@ __global__ void __launch_bounds__(BLOCK)
                     p[u] = __ldcs(reinterpret_cast<const ulonglong2*>(pairs + start) + (w * U + u) * BLOCK + threadIdx.x);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    rank[lo32(p[u].x)] = (int32_t)hi32(p[u].x);
-                    rank[lo32(p[u].y)] = (int32_t)hi32(p[u].y);
+                    // ids come from the scatter and are < n; the checks only keep
+                    // a corrupted pair from writing outside rank
+                    if (lo32(p[u].x) < (uint64_t)n) rank[lo32(p[u].x)] = (int32_t)hi32(p[u].x);
+                    if (lo32(p[u].y) < (uint64_t)n) rank[lo32(p[u].y)] = (int32_t)hi32(p[u].y);
                 }
             }
         } else {
             for (int64_t i = start + threadIdx.x; i < end; i += BLOCK) {
                 const uint64_t p = pairs[i];
-                rank[lo32(p)] = (int32_t)hi32(p);
+                if (lo32(p) < (uint64_t)n) rank[lo32(p)] = (int32_t)hi32(p);
             }
         }
     }

@@ -350,10 +350,11 @@ lrcc_status lr_rank_locked(Ctx* c, const int32_t* succ, int64_t n, int32_t head,
 // cc_label on device buffers, with the context's lock held.
 lrcc_status cc_label_locked(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label) {
     const Plan p = plan_for(KIND_CC, n);
-    lrcc_status st = ensure_ws(c, cc_ws(m));
+    const bool sv = p.cc_hook == 4;
+    lrcc_status st = ensure_ws(c, sv ? cc_sv_ws(n) : cc_ws(m));
     if (st != LRCC_OK) return st;
     reset_ctl(c, c->stream);
-    st = cc_run(c, src, dst, m, n, label, p);
+    st = sv ? cc_run_sv(c, src, dst, m, n, label, p) : cc_run(c, src, dst, m, n, label, p);
     c->last_kind = KIND_CC;
     return st;
 }
@@ -558,7 +559,7 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
     if (plan->rs_small < 0 || plan->rs_small > 16384 || plan->rs_spacing0 < 0 || plan->rs_spacing < 0 ||
         (plan->rs_spacing0 > 0 && plan->rs_spacing0 < 2) || (plan->rs_spacing > 0 && plan->rs_spacing < 2) ||
         (plan->rs_small > 0 && plan->rs_small < 1024) || plan->rs_chains < 0 || plan->rs_chains > 4 ||
-        plan->cc_hook < 0 || plan->cc_hook > 3 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
+        plan->cc_hook < 0 || plan->cc_hook > 4 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
         plan->use_graphs > 2 || plan->rs_level0 < 0 || plan->rs_level0 > 2 || plan->cc_sample < -1 ||
         plan->cc_sample > 1024)
         return LRCC_ERR_ARG;
@@ -685,7 +686,7 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
             return n > p.rs_small ? (int64_t)rs_layout(n, p, 152 * 8).bytes : 0;
         }
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
-        case KIND_CC: return (int64_t)cc_ws(m);
+        case KIND_CC: return (int64_t)(p.cc_hook == 4 ? cc_sv_ws(n) : cc_ws(m));
         case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n, m);   // n = total elements, m = lists
         case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m, n);   // n = total edges, m = graphs
         default: return -1;

@@ -97,7 +97,17 @@ def test_plan_table_roundtrip(lib):
     with pytest.raises(lrcc.LrccError):
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_small=100000)
     with pytest.raises(lrcc.LrccError):
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=4)
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=5)
+    with pytest.raises(lrcc.LrccError):
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=-2)
+    # the Shiloach-Vishkin rounds keep one int32 mark per vertex, the other rules active-edge buffers
+    L = lrcc.load()
+    before = lrcc.get_plan(lrcc.KIND_CC, 1 << 20)["cc_hook"]
+    lrcc.set_plan(lrcc.KIND_CC, 20, 20, cc_hook=4)
+    try:
+        assert L.lrcc_workspace_query(lrcc.KIND_CC, 1 << 20, 1 << 22) == 4 * (1 << 20)
+    finally:
+        lrcc.set_plan(lrcc.KIND_CC, 20, 20, cc_hook=before)
 
 
 def test_workspace_query(lib):

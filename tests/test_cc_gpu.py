@@ -24,7 +24,7 @@ def _run(src, dst, n):
     return lab.cpu().numpy()
 
 
-@pytest.fixture(params=[1, 2, 3], ids=["hook-once", "hook-relink", "hook-once-then-relink"])
+@pytest.fixture(params=[1, 2, 3, 4], ids=["hook-once", "hook-relink", "hook-once-then-relink", "shiloach-vishkin"])
 def hook(request):
     base = lrcc.get_plan(lrcc.KIND_CC, 1 << 20)["cc_hook"]
     lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=request.param)
@@ -151,6 +151,28 @@ def test_sample_pass_keeps_labels(hook, sample):
         assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
     finally:
         lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=base)
+
+
+@pytest.mark.parametrize("family", ["lists", "trees-2", "trees-5", "trees-20", "density-0.001", "density-0.01"])
+def test_paper_graph_families(hook, family):
+    # the families of the paper's component experiments (Sec. 4): collections of
+    # random lists, random trees of degree k, random graphs of edge density d;
+    # labels against the oracle, and the Shiloach-Vishkin rounds within their
+    # bound floor(log_{3/2} n) + 2
+    m = 200_000
+    if family == "lists":
+        src, dst, n = gen.list_graph(4, m // 4 + 1, 51)
+    elif family.startswith("trees"):
+        k = int(family.split("-")[1])
+        src, dst, n = gen.tree_graph(4, m // 4 + 1, k, 52)
+    else:
+        d = float(family.split("-")[1])
+        n = gen.density_vertices(m, d)
+        src, dst = gen.er(n, m, 53)
+    assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
+    if hook == 4:
+        bound = int(np.floor(np.log(n) / np.log(1.5))) + 2
+        assert lrcc.last_stats()["rounds"] <= bound
 
 
 @pytest.mark.slow

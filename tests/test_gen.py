@@ -2,8 +2,10 @@
 from __future__ import annotations
 
 import numpy as np
+import pytest
 
 import gen
+import oracle
 from gen import workloads
 
 
@@ -66,3 +68,39 @@ def test_jobs_stream():
     assert abs(np.diff(arr).mean() - 0.001) < 0.0001
     assert abs((kind == 0).mean() - 0.7) < 0.02
     assert size.min() >= 1024 and size.max() < (1 << 24)
+
+
+def test_list_graph_family():
+    count, size = 7, 300
+    src, dst, n = gen.list_graph(count, size, 3)
+    assert n == count * size and len(src) == count * (size - 1)
+    ids = np.concatenate([src, dst])
+    assert ids.min() >= 0 and ids.max() < n
+    # every vertex has degree <= 2, and exactly 2 * count path ends have degree 1
+    deg = np.bincount(ids, minlength=n)
+    assert deg.max() <= 2 and (deg == 1).sum() == 2 * count and (deg == 0).sum() == 0
+    lab = oracle.cc_uf(src, dst, n)
+    _, comp_sizes = np.unique(lab, return_counts=True)
+    assert len(comp_sizes) == count and (comp_sizes == size).all()
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_tree_graph_family(k):
+    count, size = 5, 400
+    src, dst, n = gen.tree_graph(count, size, k, 4)
+    assert n == count * size and len(src) == count * (size - 1)
+    # a forest of `count` trees of `size` vertices: n - count edges, count components
+    lab = oracle.cc_uf(src, dst, n)
+    _, comp_sizes = np.unique(lab, return_counts=True)
+    assert len(comp_sizes) == count and (comp_sizes == size).all()
+    # edges point child -> parent: every vertex is a child at most once, a parent at most k times
+    assert np.bincount(src, minlength=n).max() == 1
+    assert np.bincount(dst, minlength=n).max() <= k
+    if k == 1:
+        assert np.bincount(dst, minlength=n).max() == 1   # degree 1: the trees are paths
+
+
+def test_density_vertices():
+    assert gen.density_vertices(8_000_000, 0.001) == 126492
+    n = gen.density_vertices(10_000, 0.01)
+    assert abs(10_000 / (n * (n - 1) / 2) - 0.01) < 2e-4

@@ -47,10 +47,13 @@ def _load():
             i64, p, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32
             lib.oracle_lr_rank.argtypes = [p, i64, i32, p]
             lib.oracle_lr_rank_batched.argtypes = [p, p, p, i64, p]
+            lib.oracle_lr_scan.argtypes = [p, p, i64, i32, p]
+            lib.oracle_lr_scan_forest.argtypes = [p, p, i64, p]
             lib.oracle_cc_bfs.argtypes = [p, p, i64, i64, p]
             lib.oracle_cc_uf.argtypes = [p, p, i64, i64, p]
             lib.oracle_cc_batched.argtypes = [p, p, p, p, i64, p, ctypes.c_int]
-            for f in (lib.oracle_lr_rank, lib.oracle_lr_rank_batched, lib.oracle_cc_bfs,
+            for f in (lib.oracle_lr_rank, lib.oracle_lr_rank_batched, lib.oracle_lr_scan,
+                      lib.oracle_lr_scan_forest, lib.oracle_cc_bfs,
                       lib.oracle_cc_uf, lib.oracle_cc_batched):
                 f.restype = ctypes.c_int
             _lib = lib
@@ -78,6 +81,22 @@ def lr_rank(succ, head: int) -> np.ndarray:
     rank = np.empty(len(succ), np.int32)
     _check(_load().oracle_lr_rank(_p(succ), len(succ), int(head), _p(rank)), "lr_rank")
     return rank
+
+
+def lr_scan(succ, val, head: int) -> np.ndarray:
+    """Weighted ranks: sum of val from each element to its tail, inclusive, modulo 2^32."""
+    succ, val = _i32(succ), _i32(val)
+    out = np.empty(len(succ), np.int32)
+    _check(_load().oracle_lr_scan(_p(succ), _p(val), len(succ), int(head), _p(out)), "lr_scan")
+    return out
+
+
+def lr_scan_forest(succ, val) -> np.ndarray:
+    """lr_scan for every list of a forest of lists (heads found by in-degree)."""
+    succ, val = _i32(succ), _i32(val)
+    out = np.empty(len(succ), np.int32)
+    _check(_load().oracle_lr_scan_forest(_p(succ), _p(val), len(succ), _p(out)), "lr_scan_forest")
+    return out
 
 
 def lr_rank_batched(succ, node_off, heads) -> np.ndarray:

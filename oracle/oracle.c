@@ -11,6 +11,9 @@
  *  - List ranking (Sec. 3): a linked list is given as a successor array; the
  *    rank of an element is its distance to the last element of the list. The
  *    oracle walks the list once from its head and numbers the elements.
+ *  - Weighted list ranking (Sec. 3.2, the sublist value sum in place of the
+ *    length): the sum of per-element values from an element to its tail, for
+ *    one list or for every list of a forest (heads found by in-degree).
  *  - Connected components (Sec. 4): for an undirected graph given as an edge
  *    list, two vertices share a label iff they are joined by a path. The label
  *    of a component is its smallest vertex id. Two independent computations
@@ -23,7 +26,10 @@
  * Return codes: 0 = OK, 1 = bad argument, 4 = the input is not a single list
  * (or an edge endpoint is out of range).
  *
- * Parity pins: list ranks are checked against the closed form of the
+ * Parity pins: weighted ranks against a reversed cumulative sum over the
+ * generator's layout, brute force over small layouts and small forests (whose
+ * count is a sum of Lah numbers) and hand-worked fixtures; list ranks are
+ * checked against the closed form of the
  * generator's layout, brute force over all small layouts and the invariants
  * rank[tail] = 0, rank[i] = rank[succ[i]] + 1; component labels are checked
  * between the two oracles, against brute force on every graph with five
@@ -64,6 +70,92 @@ int oracle_lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank) 
     if (k + 1 != n) return ORC_INVALID;                 /* not every element is on the list */
     for (int64_t i = 0; i < n; ++i) rank[i] = (int32_t)(n - 1 - rank[i]);
     return ORC_OK;
+}
+
+/*
+ * Weighted list ranking (the generalisation the paper's Sec. 3.2 notes: the
+ * sublist value sum replaces the sublist length): out[i] is the sum of val[j]
+ * over the elements j from i to the tail of its list, both included. Sums are
+ * taken modulo 2^32 (unsigned arithmetic, stored as int32), which is exact
+ * whenever the true sums fit in an int32. With val = 1 everywhere, out = rank + 1.
+ *
+ * One list with a given head: one walk from the head records the order, then
+ * the sums are accumulated from the tail back to the head.
+ */
+int oracle_lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t head, int32_t* out) {
+    if (n < 0) return ORC_ARG;
+    if (n == 0) return ORC_OK;
+    if (head < 0 || head >= n) return ORC_ARG;
+    int32_t* order = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!order) return ORC_ARG;
+    for (int64_t i = 0; i < n; ++i) out[i] = 0;
+    /* out[] doubles as a visited mark during the walk (1 = visited) */
+    int64_t k = 0;
+    int64_t cur = head;
+    int rc = ORC_OK;
+    for (;;) {
+        if (out[cur]) { rc = ORC_INVALID; break; }        /* cycle */
+        out[cur] = 1;
+        order[k++] = (int32_t)cur;
+        int64_t nxt = succ[cur];
+        if (nxt == -1 || nxt == cur) break;                /* tail */
+        if (nxt < 0 || nxt >= n) { rc = ORC_INVALID; break; }
+        cur = nxt;
+    }
+    if (rc == ORC_OK && k != n) rc = ORC_INVALID;          /* not every element is on the list */
+    if (rc == ORC_OK) {
+        uint32_t acc = 0;
+        for (int64_t j = n - 1; j >= 0; --j) {
+            acc += (uint32_t)val[order[j]];
+            out[order[j]] = (int32_t)acc;
+        }
+    }
+    free(order);
+    return rc;
+}
+
+/*
+ * Weighted list ranking of a forest of lists (every element belongs to
+ * exactly one list; no head is given). An in-degree count finds the heads
+ * (elements that no successor names); any element named twice, or elements
+ * left over after walking every list from its head (a cycle), make the input
+ * invalid. Each list is then summed as in oracle_lr_scan.
+ */
+int oracle_lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, int32_t* out) {
+    if (n < 0) return ORC_ARG;
+    if (n == 0) return ORC_OK;
+    int32_t* indeg = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+    int32_t* order = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!indeg || !order) { free(indeg); free(order); return ORC_ARG; }
+    int rc = ORC_OK;
+    for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+        int64_t nxt = succ[i];
+        if (nxt == -1 || nxt == i) continue;
+        if (nxt < 0 || nxt >= n) { rc = ORC_INVALID; break; }
+        if (++indeg[nxt] > 1) rc = ORC_INVALID;            /* two predecessors */
+    }
+    int64_t seen = 0;
+    for (int64_t h = 0; h < n && rc == ORC_OK; ++h) {
+        if (indeg[h] != 0) continue;                        /* not a head */
+        int64_t k = 0;
+        int64_t cur = h;
+        for (;;) {
+            order[k++] = (int32_t)cur;
+            int64_t nxt = succ[cur];
+            if (nxt == -1 || nxt == cur) break;
+            cur = nxt;
+        }
+        uint32_t acc = 0;
+        for (int64_t j = k - 1; j >= 0; --j) {
+            acc += (uint32_t)val[order[j]];
+            out[order[j]] = (int32_t)acc;
+        }
+        seen += k;
+    }
+    if (rc == ORC_OK && seen != n) rc = ORC_INVALID;       /* elements on cycles have no head */
+    free(indeg);
+    free(order);
+    return rc;
 }
 
 /*

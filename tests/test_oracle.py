@@ -101,6 +101,146 @@ def test_lr_pins_reject_mutants():
             pins.lr_invariants(succ, head, bad)
 
 
+# ---------------------------------------------------- weighted list ranks --
+
+def test_lr_scan_golden():
+    g = _read_golden("lr_scan_small.txt")
+    assert np.array_equal(oracle.lr_scan(g["succ"], g["val"], int(g["head"][0])), g["out"])
+    assert np.array_equal(oracle.lr_scan_forest(g["forest_succ"], g["forest_val"]), g["forest_out"])
+
+
+def _suffix_sums_by_layout(perm, val):
+    # the k-th list element is stored at perm[k]: out[perm[k]] = sum of val[perm[j]] for j >= k,
+    # taken modulo 2^32 by numpy's uint32 arithmetic (a reversed cumulative sum, no walk)
+    v = val[perm].astype(np.uint32)
+    suf = np.cumsum(v[::-1], dtype=np.uint32)[::-1]
+    out = np.empty(len(perm), np.int32)
+    out[perm] = suf.view(np.int32)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 100, 65537])
+def test_lr_scan_closed_form(n):
+    succ, head, perm = gen.list_random(n, 23, with_perm=True)
+    rng = np.random.default_rng(n)
+    val = rng.integers(-1000, 1000, n).astype(np.int32)
+    assert np.array_equal(oracle.lr_scan(succ, val, head), _suffix_sums_by_layout(perm, val))
+    # unit values: one more than the rank (distance to the tail)
+    ones = np.ones(n, np.int32)
+    expect = np.empty(n, np.int32)
+    expect[perm] = np.arange(n, 0, -1, dtype=np.int32)
+    assert np.array_equal(oracle.lr_scan(succ, ones, head), expect)
+
+
+def test_lr_scan_wraps_modulo_2_32():
+    n = 1000
+    succ, head, perm = gen.list_random(n, 24, with_perm=True)
+    val = np.full(n, 2**31 - 7, np.int32)          # the true sums overflow int32 at once
+    out = oracle.lr_scan(succ, val, head)
+    assert np.array_equal(out, _suffix_sums_by_layout(perm, val))
+    k = np.arange(1, n + 1, dtype=np.uint64)
+    expect = ((k * (2**31 - 7)) % 2**32).astype(np.uint32).view(np.int32)
+    assert np.array_equal(out[perm], expect[::-1])
+
+
+def _sum_along_path(succ, val, i):
+    t = int(val[i])
+    while succ[i] != -1 and succ[i] != i:
+        i = succ[i]
+        t += int(val[i])
+    return t
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_lr_scan_brute_force_all_layouts(n):
+    # every storage layout, sums by following links from each element
+    val = np.array([3, -1, 4, 1, -5, 9][:n], np.int32)
+    for order in itertools.permutations(range(n)):
+        succ = np.full(n, -1, np.int32)
+        for a, b in zip(order, order[1:]):
+            succ[a] = b
+        out = oracle.lr_scan(succ, val, order[0])
+        assert out.tolist() == [_sum_along_path(succ, val, i) for i in range(n)]
+
+
+@pytest.mark.parametrize("sizes", [[1], [5, 1, 1], [1000, 3, 77, 1, 2], [1] * 50])
+def test_lr_scan_forest_closed_form(sizes):
+    # a forest: one random permutation cut into consecutive pieces, each piece one list
+    n = sum(sizes)
+    perm = gen.permutation(n, 25)
+    succ = np.full(n, -1, np.int32)
+    val = np.random.default_rng(n).integers(-50, 50, n).astype(np.int32)
+    expect = np.empty(n, np.int32)
+    at = 0
+    for sz in sizes:
+        piece = perm[at:at + sz]
+        succ[piece[:-1]] = piece[1:]
+        expect[piece] = _suffix_sums_by_layout(np.arange(sz), val[piece])
+        at += sz
+    assert np.array_equal(oracle.lr_scan_forest(succ, val), expect)
+    # with one piece it is the single-list function
+    if len(sizes) == 1:
+        assert np.array_equal(oracle.lr_scan(succ, val, int(perm[0])), expect)
+
+
+def test_lr_scan_brute_force_small_forests():
+    # every successor array on 5 elements that forms a forest of lists
+    n = 5
+    val = np.array([2, -3, 5, 7, 11], np.int32)
+    forests = 0
+    for succ_t in itertools.product(range(-1, n), repeat=n):
+        succ = np.array(succ_t, np.int32)
+        named = succ[(succ != -1) & (succ != np.arange(n))]
+        # a forest of lists: no element named twice, and no cycle
+        ok = len(set(named.tolist())) == len(named)
+        if ok:
+            for i in range(n):
+                j, steps = i, 0
+                while succ[j] != -1 and succ[j] != j and steps <= n:
+                    j, steps = succ[j], steps + 1
+                ok &= steps <= n
+        if not ok:
+            with pytest.raises(oracle.OracleInvalid):
+                oracle.lr_scan_forest(succ, val)
+            continue
+        forests += 1
+        out = oracle.lr_scan_forest(succ, val)
+        assert out.tolist() == [_sum_along_path(succ, val, i) for i in range(n)]
+    # forests of k labelled lists on 5 elements: Lah number L(5, k); each tail written as -1 or
+    # as a self-loop: sum_k L(5, k) 2^k = 120*2 + 240*4 + 120*8 + 20*16 + 1*32
+    assert forests == 2512
+
+
+@pytest.mark.parametrize("succ", [
+    [1, 0],                      # cycle
+    [2, 2, -1],                  # two predecessors
+    [1, 2, 0, -1],               # cycle next to a list
+    [5, -1],                     # out of range
+])
+def test_lr_scan_invalid(succ):
+    s = np.array(succ, np.int32)
+    v = np.ones(len(succ), np.int32)
+    with pytest.raises(oracle.OracleInvalid):
+        oracle.lr_scan_forest(s, v)
+    with pytest.raises(oracle.OracleInvalid):
+        oracle.lr_scan(s, v, 0)
+    with pytest.raises(oracle.OracleInvalid):
+        oracle.lr_scan(np.array([1, -1, -1], np.int32), np.ones(3, np.int32), 0)   # two lists
+
+
+def test_lr_scan_pins_reject_mutants():
+    # plausible mistakes (exclusive sums, prefix instead of suffix, a lost wrap) fail the closed form
+    n = 500
+    succ, head, perm = gen.list_random(n, 26, with_perm=True)
+    val = np.random.default_rng(3).integers(1, 100, n).astype(np.int32)
+    expect = _suffix_sums_by_layout(perm, val)
+    exclusive = expect - val
+    prefix = np.empty(n, np.int32)
+    prefix[perm] = np.cumsum(val[perm])
+    for bad in (exclusive, prefix, expect + 1):
+        assert not np.array_equal(bad, oracle.lr_scan(succ, val, head))
+
+
 # ------------------------------------------------------------ components --
 
 def test_cc_golden():

@@ -97,6 +97,35 @@ lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t
 lrcc_status lr_rank_noalloc(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
 
 /*
+ * Weighted list ranking (Sec. 3.2 notes that the method generalises by
+ * replacing each sublist's length with the sum of its values).
+ *
+ *   succ, head   one list, as for lr_rank
+ *   val  int32[n]  a value per element
+ *   out  int32[n]  output: out[i] = sum of val[j] over the elements j from i
+ *                  to the tail, both included. With val = 1, out = rank + 1.
+ *
+ * Same method as lr_rank (the walk sums values instead of counting), always
+ * with the in-place first level. The partial sums live in the 31-bit fields of
+ * the packed walk words, so the values must be non-negative with a total
+ * below 2^31; otherwise the call records LRCC_ERR_INVALID_INPUT (and leaves
+ * out undefined). Other errors as for lr_rank.
+ */
+lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t head, int32_t* out,
+                    void* stream);
+
+/*
+ * Weighted list ranking of a forest of lists: succ holds any number of
+ * disjoint lists covering all n elements (tails -1 or self-loops; no head is
+ * given), and out[i] is the sum of val from i to the tail of i's own list,
+ * modulo 2^32. Computed by pointer jumping over all lists at once (Sec. 3.1,
+ * ceil(log2 n) rounds, O(n log n) work). An element named by two successors,
+ * a cycle or a successor out of range records LRCC_ERR_INVALID_INPUT.
+ * Workspace: 16 bytes per element plus one bit.
+ */
+lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, int32_t* out, void* stream);
+
+/*
  * Connected components (Sec. 4, Algorithm 4, after Shiloach and Vishkin) of
  * an undirected graph given as an edge list.
  *
@@ -185,7 +214,8 @@ lrcc_status lrcc_last_status(void* stream);
 
 /* Statistics of the most recent call on `stream` (waits for the stream). */
 typedef struct lrcc_stats {
-    int32_t kind;            /* 1 = lr_rank, 2 = lr_rank_wyllie, 3 = cc_label, 4/5 = batched */
+    int32_t kind;            /* 1 = lr_rank, 2 = lr_rank_wyllie, 3 = cc_label, 4/5 = batched,
+                                6 = lr_scan, 7 = lr_scan_forest */
     int32_t levels;          /* lr_rank: ruling-set levels before the one-block rank */
     int64_t splitters[8];    /* lr_rank: splitters chosen at each level */
     int32_t rounds;          /* cc_label: hook passes (including the final, quiet one) */

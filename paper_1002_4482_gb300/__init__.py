@@ -30,7 +30,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIME
 KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
-           "lr_rank_host", "cc_label_host",
+           "lr_rank_host", "cc_label_host", "lr_scan", "lr_scan_forest",
            "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "cc_label_batched_sized", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
@@ -79,6 +79,8 @@ def load() -> ctypes.CDLL:
         lib.lr_rank_noalloc.argtypes = [p, i64, i32, p, p]
         lib.cc_label.argtypes = [p, p, i64, i64, p, p]
         lib.lr_rank_host.argtypes = [p, i64, i32, p, p]
+        lib.lr_scan.argtypes = [p, p, i64, i32, p, p]
+        lib.lr_scan_forest.argtypes = [p, p, i64, p, p]
         lib.cc_label_host.argtypes = [p, p, i64, i64, p, p]
         lib.lr_rank_batched.argtypes = [p, p, p, i64, p, p]
         lib.lr_rank_batched_sized.argtypes = [p, p, p, i64, i64, p, p]
@@ -100,6 +102,7 @@ def load() -> ctypes.CDLL:
         lib.lrcc_set_l2_fetch_granularity.argtypes = [i]
         lib.lrcc_get_l2_fetch_granularity.restype = i
         for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_host", "cc_label_host",
+                  "lr_scan", "lr_scan_forest",
                   "lr_rank_batched",
                   "lr_rank_batched_sized",
                   "cc_label_batched", "cc_label_batched_sized",
@@ -182,6 +185,32 @@ def lr_rank_wyllie(succ: torch.Tensor, head: int, out: torch.Tensor | None = Non
     _call(load().lr_rank_wyllie(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), _stream(stream)),
           "lr_rank_wyllie")
     return rank
+
+
+def lr_scan(succ: torch.Tensor, val: torch.Tensor, head: int, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """Weighted ranks: sum of ``val`` from each element to the tail, inclusive, modulo 2^32."""
+    _dev_i32(succ, "succ")
+    _dev_i32(val, "val")
+    if val.numel() != succ.numel():
+        raise ValueError("val must have one entry per element")
+    res = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_scan(succ.data_ptr(), val.data_ptr(), succ.numel(), int(head), res.data_ptr(), _stream(stream)),
+          "lr_scan")
+    return res
+
+
+def lr_scan_forest(succ: torch.Tensor, val: torch.Tensor, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """:func:`lr_scan` for every list of a forest of lists (no head given)."""
+    _dev_i32(succ, "succ")
+    _dev_i32(val, "val")
+    if val.numel() != succ.numel():
+        raise ValueError("val must have one entry per element")
+    res = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_scan_forest(succ.data_ptr(), val.data_ptr(), succ.numel(), res.data_ptr(), _stream(stream)),
+          "lr_scan_forest")
+    return res
 
 
 def lr_rank_noalloc(succ: torch.Tensor, head: int, out: torch.Tensor, stream=None) -> torch.Tensor:

@@ -8,7 +8,7 @@ namespace lrcc {
 
 // val[j] += val[nxt[j]], nxt[j] = nxt[nxt[j]] for every j < r until no link
 // is left; on return val[j] is the sum of val over j and every element after
-// it. THREADS threads each own PER elements (r <= PER * THREADS). Rounds are
+// it (modulo 2^32). THREADS threads each own PER elements (r <= PER * THREADS). Rounds are
 // capped at ceil(log2 r) + 2; a list that still has links then contains a
 // cycle, which is recorded as invalid input.
 template <int PER, int THREADS>
@@ -28,7 +28,7 @@ __device__ void block_wyllie(int* val, int* nxt, int r, DevCtl* ctl) {
                 const int x = nxt[j];
                 nv[q] = val[j];
                 if (x != (int)NIL) {
-                    nv[q] += val[x];
+                    nv[q] = (int)((unsigned)nv[q] + (unsigned)val[x]);   // sums modulo 2^32
                     nn[q] = nxt[x];
                     any = true;
                 }

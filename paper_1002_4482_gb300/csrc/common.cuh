@@ -29,7 +29,9 @@ struct DevCtl {
     int cc_stop;         // component loop: the last pass joined nothing
     int seg_next;        // batched union path: next edge slice of the current pass
     int seg_next_v;      // batched union path: next vertex slice of the current shortcut
-    int pad[3];
+    int scan_bad;        // weighted ranks: the values are outside the supported range; skip the work
+    int pad[2];
+    unsigned long long scan_total;   // weighted ranks: sum of the values
 };
 
 __device__ __forceinline__ void record_error(DevCtl* c, int code, int where = -1) {

@@ -35,26 +35,37 @@ __device__ __forceinline__ void cta_wyllie(int* val, int* nxt, int r, DevCtl* ct
     block_wyllie<PER, FINAL_THREADS>(val, nxt, r, ctl);
 }
 
-// One block ranks a whole list of n <= PER * FINAL_THREADS elements.
+// One block ranks a whole list of n <= PER * FINAL_THREADS elements. With
+// weights (w != nullptr) it writes the inclusive suffix sums of w instead of
+// the ranks, after a first pass with unit weights that checks the list.
 template <int PER>
 __global__ void __launch_bounds__(FINAL_THREADS, 1)
-    lr_small_kernel(const int32_t* __restrict__ succ, int n, int head, int32_t* __restrict__ rank,
-                    DevCtl* ctl) {
+    lr_small_kernel(const int32_t* __restrict__ succ, const int32_t* __restrict__ w, int n, int head,
+                    int32_t* __restrict__ rank, DevCtl* ctl) {
     extern __shared__ int sm[];
     int* val = sm;
     int* nxt = sm + PER * FINAL_THREADS;
-    for (int i = threadIdx.x; i < n; i += FINAL_THREADS) {
-        const int s = succ[i];
-        const bool tail = (s == -1) | (s == i);
-        const bool bad = !tail && (s < 0 || s >= n);
-        if (bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, i);
-        nxt[i] = (tail || bad) ? (int)NIL : s;
-        val[i] = 1;
-    }
-    __syncthreads();
+    auto load = [&](bool weighted) {
+        for (int i = threadIdx.x; i < n; i += FINAL_THREADS) {
+            const int s = succ[i];
+            const bool tail = (s == -1) | (s == i);
+            const bool bad = !tail && (s < 0 || s >= n);
+            if (bad && !weighted) record_error(ctl, LRCC_ERR_INVALID_INPUT, i);
+            nxt[i] = (tail || bad) ? (int)NIL : s;
+            val[i] = weighted ? w[i] : 1;
+        }
+        __syncthreads();
+    };
+    load(false);
     cta_wyllie<PER>(val, nxt, n, ctl);
-    for (int i = threadIdx.x; i < n; i += FINAL_THREADS) rank[i] = val[i] - 1;
     if (threadIdx.x == 0 && val[head] != n) record_error(ctl, LRCC_ERR_INVALID_INPUT, head);
+    if (w) {
+        __syncthreads();
+        load(true);
+        cta_wyllie<PER>(val, nxt, n, ctl);
+    }
+    const int bias = w ? 0 : 1;
+    for (int i = threadIdx.x; i < n; i += FINAL_THREADS) rank[i] = val[i] - bias;
 }
 
 // Last ruling-set level: one block ranks the weighted list of splitters held
@@ -64,9 +75,24 @@ template <int PER>
 __global__ void __launch_bounds__(FINAL_THREADS, 1)
     rs_final_kernel(const uint64_t* __restrict__ R, int r, int32_t* __restrict__ S, int64_t expect,
                     DevCtl* ctl) {
+    if (ctl->scan_bad) return;
     extern __shared__ int sm[];
     int* val = sm;
     int* nxt = sm + PER * FINAL_THREADS;
+    // the splitters must form one list headed by splitter 0: every other
+    // splitter has exactly one predecessor, splitter 0 none (this also covers
+    // weighted sums, where the head's total says nothing about the count)
+    for (int j = threadIdx.x; j < r; j += FINAL_THREADS) val[j] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += FINAL_THREADS) {
+        const uint32_t nx = lo32(R[j]);
+        if (nx < (uint32_t)r) atomicAdd(&val[nx], 1);
+        else if (nx != NIL) record_error(ctl, LRCC_ERR_INVALID_INPUT, -3);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += FINAL_THREADS)
+        if (val[j] != (j == 0 ? 0 : 1)) record_error(ctl, LRCC_ERR_INVALID_INPUT, -3);
+    __syncthreads();
     for (int j = threadIdx.x; j < r; j += FINAL_THREADS) {
         const uint64_t w = R[j];
         nxt[j] = (int)lo32(w);
@@ -89,14 +115,16 @@ __global__ void __launch_bounds__(FINAL_THREADS, 1)
 // Offsets come from the MurmurHash3 finaliser of (block, seed).
 
 // Level-0 select: one streaming pass packs succ into walk words
-// W[i] = (next | SPL, splitter index) for splitters, (next, weight 1) for the
-// rest, and records each splitter's successor and weight. Warps stride over
+// W[i] = (next | SPL, splitter index) for splitters, (next, weight) for the
+// rest (weight 1, or the element's value for weighted sums), and records each
+// splitter's successor and weight. Warps stride over
 // groups of 4 elements (Sec. 2.5), with 16-byte loads and stores.
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK)
-    rs_select0(const int32_t* __restrict__ succ, int64_t n, int32_t head, uint64_t* __restrict__ W,
-               int32_t* __restrict__ snext, int32_t* __restrict__ sw, int logD, int64_t nb, uint32_t seed,
-               DevCtl* ctl) {
+    rs_select0(const int32_t* __restrict__ succ, const int32_t* __restrict__ val, int64_t n, int32_t head,
+               uint64_t* __restrict__ W, int32_t* __restrict__ snext, int32_t* __restrict__ sw, int logD,
+               int64_t nb, uint32_t seed, DevCtl* ctl) {
+    if (ctl->scan_bad) return;
     const uint64_t pol = policy_evict_first();
     const int64_t D = int64_t(1) << logD;
     const int64_t bh = head >> logD;
@@ -104,13 +132,20 @@ __global__ void __launch_bounds__(BLOCK)
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
          g += static_cast<int64_t>(gridDim.x) * BLOCK) {
         const int64_t i0 = g * 4;
-        int s[4];
+        int s[4], wt[4] = {1, 1, 1, 1};
         if (VEC && i0 + 3 < n) {
             const int4 v = ld_stream_v4(succ + i0, pol);
             s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+            if (val) {
+                const int4 x = ld_stream_v4(val + i0, pol);
+                wt[0] = x.x; wt[1] = x.y; wt[2] = x.z; wt[3] = x.w;
+            }
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s[q] = (i0 + q < n) ? ld_stream(succ + i0 + q, pol) : -1;
+            for (int q = 0; q < 4; ++q) {
+                s[q] = (i0 + q < n) ? ld_stream(succ + i0 + q, pol) : -1;
+                if (val && i0 + q < n) wt[q] = ld_stream(val + i0 + q, pol);
+            }
         }
         // D >= 4 and i0 % 4 == 0, so the 4 elements share one block
         const int64_t b = i0 >> logD;
@@ -129,9 +164,9 @@ __global__ void __launch_bounds__(BLOCK)
             if (i < n && (uint32_t)(i - (b << logD)) == off) {
                 w[q] = pack(nx | SPL, (uint32_t)j);
                 snext[j] = (int32_t)nx;
-                sw[j] = 1;
+                sw[j] = wt[q];
             } else {
-                w[q] = pack(nx, 1);
+                w[q] = pack(nx, (uint32_t)wt[q]);
             }
         }
         if (i0 + 3 < n) {
@@ -152,7 +187,8 @@ __global__ void __launch_bounds__(BLOCK)
 // (next | SPL, block) and records its successor and weight.
 __global__ void __launch_bounds__(BLOCK)
     rs_select(uint64_t* __restrict__ R, int64_t nl, int32_t* __restrict__ snext, int32_t* __restrict__ sw,
-              int logD, int64_t nb, uint32_t seed) {
+              int logD, int64_t nb, uint32_t seed, const DevCtl* ctl) {
+    if (ctl->scan_bad) return;
     const int64_t D = int64_t(1) << logD;
     for (int64_t b = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; b < nb;
          b += static_cast<int64_t>(gridDim.x) * BLOCK) {
@@ -174,6 +210,7 @@ template <int K>
 __global__ void __launch_bounds__(BLOCK)
     rs_walk(uint64_t* __restrict__ W, const int32_t* __restrict__ snext, const int32_t* __restrict__ sw,
             uint64_t* __restrict__ Rout, int r, int* work, int64_t nlevel, DevCtl* ctl) {
+    if (ctl->scan_bad) return;
     constexpr int CHUNK = 64;
     const int lane = threadIdx.x & 31;
     int pool = 0, pool_end = 0;
@@ -759,15 +796,18 @@ __global__ void __launch_bounds__(BLOCK)
 
 // Expand at level >= 1: S[c] = S_next[owner] - prefix (RS5).
 __global__ void __launch_bounds__(BLOCK)
-    rs_expand(const uint64_t* __restrict__ W, int r, const int32_t* __restrict__ Snext,
+    rs_expand(const uint64_t* __restrict__ W, int r, const int32_t* __restrict__ Snext, int rnext,
               int32_t* __restrict__ S, DevCtl* ctl) {
+    if (ctl->scan_bad) return;
     for (int c = blockIdx.x * BLOCK + threadIdx.x; c < r; c += gridDim.x * BLOCK) {
         const uint64_t w = W[c];
         const uint32_t lo = lo32(w), hi = hi32(w);
-        if (lo & SPL) {
+        // indices are checked so that a malformed input can only give wrong
+        // values (with an error recorded), never an access outside Snext
+        if ((lo & SPL) && hi < (uint32_t)rnext) {
             S[c] = Snext[hi];
-        } else if (hi & VIS) {
-            S[c] = Snext[hi & ~VIS] - (int32_t)lo;
+        } else if (!(lo & SPL) && (hi & VIS) && (hi & ~VIS) < (uint32_t)rnext) {
+            S[c] = (int32_t)((uint32_t)Snext[hi & ~VIS] - lo);
         } else {
             record_error(ctl, LRCC_ERR_INVALID_INPUT, c);
             S[c] = 0;
@@ -775,11 +815,13 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
-// Expand at level 0 into the caller's rank array: rank = S1[owner] - prefix - 1.
+// Expand at level 0 into the caller's array: rank = S1[owner] - prefix - 1
+// (bias 1); for weighted sums the inclusive suffix S1[owner] - prefix (bias 0).
 template <bool VEC>
 __global__ void __launch_bounds__(BLOCK)
-    rs_expand0(const uint64_t* __restrict__ W, int64_t n, const int32_t* __restrict__ S1,
-               int32_t* __restrict__ rank, DevCtl* ctl) {
+    rs_expand0(const uint64_t* __restrict__ W, int64_t n, const int32_t* __restrict__ S1, int64_t r1,
+               int32_t* __restrict__ rank, int bias, DevCtl* ctl) {
+    if (ctl->scan_bad) return;
     const int64_t ngroups = (n + 3) >> 2;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
          g += static_cast<int64_t>(gridDim.x) * BLOCK) {
@@ -797,10 +839,10 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t lo = lo32(w[q]), hi = hi32(w[q]);
-            if (lo & SPL) {
-                out[q] = S1[hi] - 1;
-            } else if (hi & VIS) {
-                out[q] = S1[hi & ~VIS] - (int32_t)lo - 1;
+            if ((lo & SPL) && hi < (uint64_t)r1) {
+                out[q] = S1[hi] - bias;
+            } else if (!(lo & SPL) && (hi & VIS) && (hi & ~VIS) < (uint64_t)r1) {
+                out[q] = (int32_t)((uint32_t)S1[hi & ~VIS] - lo - (uint32_t)bias);
             } else {
                 record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)(i0 + q));
                 out[q] = -1;
@@ -919,20 +961,98 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+// ------------------------------------------- range check of the values
+
+// Weighted ranks by the ruling set keep every partial sum in the 31-bit
+// fields of the packed words, whose top bits are the splitter and visited
+// flags: the values must be non-negative and their total below 2^31. This pass
+// (one streaming read of val) checks both; when they do not hold, the later
+// kernels of the call return at once and the call reports invalid input.
+__global__ void __launch_bounds__(BLOCK)
+    rs_scan_check(const int32_t* __restrict__ val, int64_t n, DevCtl* ctl) {
+    const uint64_t pol = policy_evict_first();
+    unsigned long long sum = 0;
+    bool neg = false;
+    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+        const int32_t v = ld_stream(val + i, pol);
+        neg |= v < 0;
+        sum += (unsigned long long)(uint32_t)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) ctl->scan_bad = 1;
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&ctl->scan_total, sum);
+}
+
+__global__ void rs_scan_verdict(DevCtl* ctl) {
+    if (ctl->scan_bad || ctl->scan_total >= (1ull << 31)) {
+        ctl->scan_bad = 1;
+        record_error(ctl, LRCC_ERR_INVALID_INPUT, -6);
+    }
+}
+
+// ------------------------------------------- weighted ranks of a forest
+
+// A forest of lists has no single head, so its weighted ranks are taken by
+// pointer jumping (Sec. 3.1) over every list at once: words (next or NIL,
+// value), ceil(log2 n) rounds of (next, value) <- (next[next], value +
+// value[next]). The pack pass also checks that no element is named by two
+// successors (one bit per element, set with atomicOr in a bitmap L2 holds);
+// an element still linked after the last round lies on a cycle.
+__global__ void __launch_bounds__(BLOCK)
+    fs_pack(const int32_t* __restrict__ succ, const int32_t* __restrict__ val, int64_t n, uint64_t* __restrict__ W,
+            uint32_t* named, DevCtl* ctl) {
+    const uint64_t pol = policy_evict_first();
+    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+        const int32_t sx = ld_stream(succ + i, pol);
+        const bool tail = (sx == -1) | (sx == i);
+        const bool bad = !tail && (sx < 0 || sx >= n);
+        if (bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+        if (!tail && !bad) {
+            const uint32_t bit = 1u << (sx & 31);
+            if (atomicOr(named + (sx >> 5), bit) & bit) record_error(ctl, LRCC_ERR_INVALID_INPUT, sx);
+        }
+        W[i] = pack((tail || bad) ? NIL : (uint32_t)sx, (uint32_t)ld_stream(val + i, pol));
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK)
+    fs_jump(const uint64_t* __restrict__ Win, uint64_t* __restrict__ Wout, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+        uint64_t w = Win[i];
+        const uint32_t nx = lo32(w);
+        if (nx != NIL) {
+            const uint64_t x = Win[nx];
+            w = pack(lo32(x), hi32(w) + hi32(x));
+        }
+        Wout[i] = w;
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK)
+    fs_final(const uint64_t* __restrict__ W, int64_t n, int32_t* __restrict__ out, DevCtl* ctl) {
+    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+        const uint64_t w = W[i];
+        if (lo32(w) != NIL) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+        out[i] = (int32_t)hi32(w);
+    }
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 int small_per(int n) { return n <= 4096 ? 4 : (n <= 8192 ? 8 : 16); }
 
-lrcc_status launch_small(Ctx* c, cudaStream_t s, const int32_t* succ, int n, int head, int32_t* rank) {
+lrcc_status launch_small(Ctx* c, cudaStream_t s, const int32_t* succ, int n, int head, int32_t* rank,
+                         const int32_t* val = nullptr) {
     const int per = small_per(n);
     const size_t smem = 2 * sizeof(int) * per * FINAL_THREADS;
     const void* k = per == 4 ? (const void*)lr_small_kernel<4>
                   : per == 8 ? (const void*)lr_small_kernel<8> : (const void*)lr_small_kernel<16>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     phase_begin(c, s);
-    if (per == 4) lr_small_kernel<4><<<1, FINAL_THREADS, smem, s>>>(succ, n, head, rank, c->ctl);
-    else if (per == 8) lr_small_kernel<8><<<1, FINAL_THREADS, smem, s>>>(succ, n, head, rank, c->ctl);
-    else lr_small_kernel<16><<<1, FINAL_THREADS, smem, s>>>(succ, n, head, rank, c->ctl);
+    if (per == 4) lr_small_kernel<4><<<1, FINAL_THREADS, smem, s>>>(succ, val, n, head, rank, c->ctl);
+    else if (per == 8) lr_small_kernel<8><<<1, FINAL_THREADS, smem, s>>>(succ, val, n, head, rank, c->ctl);
+    else lr_small_kernel<16><<<1, FINAL_THREADS, smem, s>>>(succ, val, n, head, rank, c->ctl);
     phase_end(c, s, PH_SMALL);
     return cuda_status(cudaGetLastError());
 }
@@ -1018,8 +1138,16 @@ size_t lr_wyllie_ws(int64_t n, const Plan&) { return 2 * align_up(sizeof(uint64_
 // ------------------------------------------------------------ enqueueing
 
 lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
-                          int32_t* rank, const Plan& p, const RsLayout& L) {
-    if (n <= p.rs_small || L.levels == 0) return launch_small(c, s, succ, (int)n, head, rank);
+                          int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val) {
+    // weighted sums use the in-place first level (the read-only one counts positions)
+    if (val && L.readonly) return LRCC_ERR_ARG;
+    if (val) {
+        phase_begin(c, s);
+        rs_scan_check<<<stream_grid(c, n, (const void*)rs_scan_check), BLOCK, 0, s>>>(val, n, c->ctl);
+        rs_scan_verdict<<<1, 1, 0, s>>>(c->ctl);
+        phase_end(c, s, PH_SELECT0);
+    }
+    if (n <= p.rs_small || L.levels == 0) return launch_small(c, s, succ, (int)n, head, rank, val);
     char* base = static_cast<char*>(c->ws);
     auto R = [&](int l) { return reinterpret_cast<uint64_t*>(base + L.off_R[l]); };
     auto SN = [&](int l) { return reinterpret_cast<int32_t*>(base + L.off_snext[l]); };
@@ -1030,16 +1158,18 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     const uint32_t seed0 = (uint32_t)(p.seed ^ (p.seed >> 32));
 
     // level 0
-    const bool vec = aligned16(succ);
+    const bool vec = aligned16(succ) && (!val || aligned16(val));
     const int64_t groups = (n + 3) / 4;
     if (!L.readonly) {
         const void* k = vec ? (const void*)rs_select0<true> : (const void*)rs_select0<false>;
         const int g = stream_grid(c, groups, k);
         phase_begin(c, s);
         if (vec)
-            rs_select0<true><<<g, BLOCK, 0, s>>>(succ, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1], seed0, ctl);
+            rs_select0<true><<<g, BLOCK, 0, s>>>(succ, val, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1],
+                                                 seed0, ctl);
         else
-            rs_select0<false><<<g, BLOCK, 0, s>>>(succ, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1], seed0, ctl);
+            rs_select0<false><<<g, BLOCK, 0, s>>>(succ, val, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1],
+                                                  seed0, ctl);
         phase_end(c, s, PH_SELECT0);
     }
     Level0 L0;
@@ -1101,7 +1231,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         const uint32_t seed = mix32(seed0 + 0x9E3779B9u * (uint32_t)l);
         const int g = stream_grid(c, L.size[l + 1], (const void*)rs_select);
         phase_begin(c, s);
-        rs_select<<<g, BLOCK, 0, s>>>(R(l), L.size[l], SN(l + 1), SW(l + 1), L.logD[l], L.size[l + 1], seed);
+        rs_select<<<g, BLOCK, 0, s>>>(R(l), L.size[l], SN(l + 1), SW(l + 1), L.logD[l], L.size[l + 1], seed, ctl);
         phase_end(c, s, PH_SELECT);
         walk(l, R(l), L.size[l]);
     }
@@ -1113,20 +1243,20 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         phase_begin(c, s);
         if (per == 4) {
             cudaFuncSetAttribute((const void*)rs_final_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            rs_final_kernel<4><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), n, ctl);
+            rs_final_kernel<4><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), val ? -1 : n, ctl);
         } else if (per == 8) {
             cudaFuncSetAttribute((const void*)rs_final_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            rs_final_kernel<8><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), n, ctl);
+            rs_final_kernel<8><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), val ? -1 : n, ctl);
         } else {
             cudaFuncSetAttribute((const void*)rs_final_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            rs_final_kernel<16><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), n, ctl);
+            rs_final_kernel<16><<<1, FINAL_THREADS, smem, s>>>(R(lf), r, S(lf), val ? -1 : n, ctl);
         }
         phase_end(c, s, PH_FINAL);
     }
     for (int l = L.levels - 1; l >= 1; --l) {
         const int g = stream_grid(c, L.size[l], (const void*)rs_expand);
         phase_begin(c, s);
-        rs_expand<<<g, BLOCK, 0, s>>>(R(l), (int)L.size[l], S(l + 1), S(l), ctl);
+        rs_expand<<<g, BLOCK, 0, s>>>(R(l), (int)L.size[l], S(l + 1), (int)L.size[l + 1], S(l), ctl);
         phase_end(c, s, PH_EXPAND);
     }
     if (L.readonly) {
@@ -1144,10 +1274,42 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         const void* k = v ? (const void*)rs_expand0<true> : (const void*)rs_expand0<false>;
         const int g = stream_grid(c, groups, k);
         phase_begin(c, s);
-        if (v) rs_expand0<true><<<g, BLOCK, 0, s>>>(W0, n, S(1), rank, ctl);
-        else rs_expand0<false><<<g, BLOCK, 0, s>>>(W0, n, S(1), rank, ctl);
+        const int bias = val ? 0 : 1;
+        if (v) rs_expand0<true><<<g, BLOCK, 0, s>>>(W0, n, S(1), L.size[1], rank, bias, ctl);
+        else rs_expand0<false><<<g, BLOCK, 0, s>>>(W0, n, S(1), L.size[1], rank, bias, ctl);
         phase_end(c, s, PH_EXPAND0);
     }
+    return cuda_status(cudaGetLastError());
+}
+
+size_t lr_scan_forest_ws(int64_t n) {
+    return 2 * align_up(sizeof(uint64_t) * (size_t)n, 256) + align_up(sizeof(uint32_t) * (size_t)((n + 31) / 32), 256);
+}
+
+lrcc_status lr_enqueue_scan_forest(Ctx* c, cudaStream_t s, const int32_t* succ, const int32_t* val, int64_t n,
+                                   int32_t* out) {
+    char* base = static_cast<char*>(c->ws);
+    uint64_t* W0 = reinterpret_cast<uint64_t*>(base);
+    uint64_t* W1 = reinterpret_cast<uint64_t*>(base + align_up(sizeof(uint64_t) * (size_t)n, 256));
+    uint32_t* named = reinterpret_cast<uint32_t*>(base + 2 * align_up(sizeof(uint64_t) * (size_t)n, 256));
+    const int g = stream_grid(c, n, (const void*)fs_jump);
+    cudaMemsetAsync(named, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
+    phase_begin(c, s);
+    fs_pack<<<g, BLOCK, 0, s>>>(succ, val, n, W0, named, c->ctl);
+    phase_end(c, s, PH_WY_PACK);
+    int rounds = 0;
+    while ((int64_t(1) << rounds) < n) ++rounds;
+    uint64_t* a = W0;
+    uint64_t* b = W1;
+    for (int r = 0; r < rounds; ++r) {
+        phase_begin(c, s);
+        fs_jump<<<g, BLOCK, 0, s>>>(a, b, n);
+        phase_end(c, s, PH_WY_JUMP);
+        std::swap(a, b);
+    }
+    phase_begin(c, s);
+    fs_final<<<g, BLOCK, 0, s>>>(a, n, out, c->ctl);
+    phase_end(c, s, PH_WY_FINAL);
     return cuda_status(cudaGetLastError());
 }
 

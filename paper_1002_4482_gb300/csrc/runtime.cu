@@ -326,22 +326,25 @@ int lrcc_version(void) { return 100; }
 namespace {
 
 // lr_rank on device buffers, with the context's lock held.
-lrcc_status lr_rank_locked(Ctx* c, const int32_t* succ, int64_t n, int32_t head, int32_t* rank) {
+lrcc_status lr_rank_locked(Ctx* c, const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
+                           const int32_t* val = nullptr) {
     lrcc_status st = LRCC_OK;
-    const Plan p = plan_for(KIND_LR, n);
+    Plan p = plan_for(KIND_LR, n);
+    if (val) p.rs_level0 = 1;   // weighted sums: the in-place first level carries the values
     const RsLayout L = rs_layout(n, p, rs_walk_grid(c, p));
     if (n > p.rs_small) {
         st = ensure_ws(c, L.bytes);
         if (st != LRCC_OK) return st;
     }
-    std::vector<uint64_t> key = {(uint64_t)KIND_LR, (uint64_t)succ, (uint64_t)n, (uint64_t)head, (uint64_t)rank};
+    std::vector<uint64_t> key = {(uint64_t)KIND_LR, (uint64_t)succ, (uint64_t)n, (uint64_t)head, (uint64_t)rank,
+                                 (uint64_t)val};
     const auto pk = plan_key(p);
     key.insert(key.end(), pk.begin(), pk.end());
     st = launch_recorded(c, p, key, [&](cudaStream_t s) {
         reset_ctl(c, s);
-        return lr_enqueue_rs(c, s, succ, n, head, rank, p, L);
+        return lr_enqueue_rs(c, s, succ, n, head, rank, p, L, val);
     });
-    c->last_kind = KIND_LR;
+    c->last_kind = val ? 6 : KIND_LR;
     c->last_levels = n > p.rs_small ? L.levels : 0;
     for (int l = 0; l < MAX_LEVELS; ++l) c->last_splitter_cap[l] = l < L.levels ? L.size[l + 1] : 0;
     return st;
@@ -372,6 +375,38 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     return lr_rank_locked(c, succ, n, head, rank);
+}
+
+lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t head, int32_t* out, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !val || !out || head < 0 || head >= n) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return lr_rank_locked(c, succ, n, head, out, val);
+}
+
+lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, int32_t* out, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !val || !out) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const Plan p = plan_for(KIND_LR_WYLLIE, n);
+    st = ensure_ws(c, lr_scan_forest_ws(n));
+    if (st != LRCC_OK) return st;
+    const std::vector<uint64_t> key = {7, (uint64_t)succ, (uint64_t)val, (uint64_t)n, (uint64_t)out};
+    st = launch_recorded(c, p, key, [&](cudaStream_t s) {
+        reset_ctl(c, s);
+        return lr_enqueue_scan_forest(c, s, succ, val, n, out);
+    });
+    c->last_kind = 7;
+    c->last_levels = 0;
+    return st;
 }
 
 lrcc_status lr_rank_host(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {

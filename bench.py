@@ -548,6 +548,28 @@ def main():
                  "lr_ordered_ms": ms_ord, "lr_ordered_mnodes_per_s": n_lr / ms_ord / 1e3}
         del osucc_d
         succ = torch.from_numpy(succ_h).to(dev)
+        # weighted ranks of the same list (values i mod 7, total below 2^31), and of a
+        # forest: the same elements cut into 4096 lists (not part of the step)
+        with torch.cuda.stream(stream):
+            val_d = (torch.arange(n_lr, device=dev, dtype=torch.int64) % 7).to(torch.int32)
+        ms_scan = timed(lambda: lrcc.lr_scan(succ, val_d, head, out=rank_out, stream=stream))
+        lrcc.check(stream)
+        # the forest: the list's order from its ranks, then a tail every n/4096 positions
+        lrcc.lr_rank(succ, head, out=rank_out, stream=stream)
+        with torch.cuda.stream(stream):
+            order = torch.empty(n_lr, dtype=torch.int64, device=dev)
+            order[(n_lr - 1 - rank_out).long()] = torch.arange(n_lr, device=dev)
+            cuts = torch.linspace(0, n_lr, 4097, device=dev, dtype=torch.float64).long()[1:]
+            fsucc = succ.clone()
+            fsucc[order[cuts - 1]] = -1
+            del order
+        ms_forest = timed(lambda: lrcc.lr_scan_forest(fsucc, val_d, out=rank_out, stream=stream), reps=2)
+        lrcc.check(stream)
+        del fsucc
+        extra.update({"lr_scan_ms": ms_scan, "lr_scan_mnodes_per_s": n_lr / ms_scan / 1e3,
+                      "lr_scan_forest_ms": ms_forest, "lr_scan_forest_lists": 4096,
+                      "lr_scan_forest_mnodes_per_s": n_lr / ms_forest / 1e3})
+        del val_d
 
     # end to end through the public API with host buffers
     e2e = None

@@ -184,18 +184,34 @@ __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n,
          g += static_cast<int64_t>(gridDim.x) * BLOCK) {
         const int64_t i0 = g * 4;
         if (VEC && i0 + 3 < n) {
-            int4 p = *reinterpret_cast<const int4*>(parent + i0);
-            int* pp = reinterpret_cast<int*>(&p);
-            bool ch = false;
+            const int4 p = *reinterpret_cast<const int4*>(parent + i0);
+            // the four chases advance together, so four loads are in flight at a time;
+            // they read through L1: roots do not move during this pass, a value read
+            // late is still an ancestor, and the hot roots of large trees then hit L1
+            // instead of queueing on one L2 slice
+            int x[4] = {p.x, p.y, p.z, p.w};
+            bool live[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (pp[q] != (int)(i0 + q)) {
-                    const int r = find_root(parent, pp[q], keep);
-                    ch |= r != pp[q];
-                    pp[q] = r;
+            for (int q = 0; q < 4; ++q) live[q] = x[q] != (int)(i0 + q);
+            bool any = live[0] | live[1] | live[2] | live[3];
+            bool ch = false;
+            while (any) {
+                int nx[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nx[q] = live[q] ? ld_hint(parent + x[q], keep) : x[q];
+                any = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (live[q] && nx[q] != x[q]) {
+                        x[q] = nx[q];
+                        ch = true;
+                        any = true;
+                    } else {
+                        live[q] = false;
+                    }
                 }
             }
-            if (ch) *reinterpret_cast<int4*>(parent + i0) = p;
+            if (ch) *reinterpret_cast<int4*>(parent + i0) = make_int4(x[0], x[1], x[2], x[3]);
         } else {
             for (int q = 0; q < 4; ++q) {
                 const int64_t v = i0 + q;

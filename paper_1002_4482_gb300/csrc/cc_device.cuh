@@ -7,10 +7,13 @@
 namespace lrcc {
 
 // Follow parents to a root. Every link goes to a smaller id, so the walk
-// ends within n steps on any state the kernels can produce.
+// ends within n steps on any state the kernels can produce. For shortcut
+// passes only: roots do not move while they run, so the loads may go through
+// L1 (a value read late is still an ancestor) and the hot roots of large
+// trees hit L1 instead of queueing on one L2 slice.
 __device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t x, uint64_t keep) {
     for (;;) {
-        const int32_t p = ld_cg_hint(parent + x, keep);
+        const int32_t p = ld_hint(parent + x, keep);
         if (p == x) return x;
         x = p;
     }

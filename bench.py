@@ -642,6 +642,16 @@ def main():
         cpu = {"value": (len(sample[0]) + len(sample[2])) / t / 1e6, "unit": UNIT, "cores": 1,
                "kind": "oracle", "sample": sample[5], "seconds": t, "lr_seconds": tl, "cc_seconds": tc,
                "host_cores": os.cpu_count()}
+        # the paper's other CPU comparison: random-splitter list ranking on every host core
+        import cpu_baseline
+        cores = os.cpu_count() or 1
+        cpu_baseline.lr_rank(sample[0], sample[1], cores)
+        t0 = time.perf_counter()
+        cpu_baseline.lr_rank(sample[0], sample[1], cores)
+        tp = time.perf_counter() - t0
+        cpu["parallel_lr"] = {"value": len(sample[0]) / tp / 1e6, "unit": "M list nodes/s", "cores": cores,
+                              "kind": "random-splitter list ranking, pthreads (cpu_baseline/)",
+                              "sample": "the same random-layout list as the oracle leg", "seconds": tp}
 
     batched = serving = None
     families = None

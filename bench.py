@@ -231,6 +231,45 @@ def random_gather_peak(torch, dev, stream, log2n=28):
     return (1 << log2n) / (ms / 1e3) / 1e9
 
 
+def bench_lr_sweep(lrcc, torch, dev, stream, sizes=(16, 18, 20, 22, 24, 26, 28)):
+    """List-ranking throughput against list size for both first-level layouts
+    (in-place 8-byte words, read-only walk with chunked records) and both list
+    layouts (random, ordered = even splitters along the list): where the rate
+    changes as the list outgrows L2 (the paper's "inflection", Sec. 3.2)."""
+    import gen
+    out = []
+    base = {k: lrcc.get_plan(lrcc.KIND_LR, 1 << k) for k in sizes}
+    try:
+        for lg in sizes:
+            n = 1 << lg
+            row = {"log2n": lg}
+            for layout in ("random", "ordered"):
+                succ_h, head = gen.list_random(n, 100 + lg) if layout == "random" else gen.list_ordered(n)
+                with torch.cuda.stream(stream):
+                    s_d = torch.from_numpy(succ_h).to(dev)
+                    r_d = torch.empty_like(s_d)
+                for l0 in (1, 2):
+                    lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=l0)
+                    lrcc.lr_rank(s_d, head, out=r_d, stream=stream)
+                    stream.synchronize()
+                    best = float("inf")
+                    for _ in range(3):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        lrcc.lr_rank(s_d, head, out=r_d, stream=stream)
+                        b.record(stream)
+                        b.synchronize()
+                        best = min(best, a.elapsed_time(b))
+                    lrcc.check(stream)
+                    row[f"{layout}_{'inplace' if l0 == 1 else 'readonly'}_gnodes_per_s"] = n / best / 1e6
+                del s_d, r_d
+            out.append(row)
+    finally:
+        for lg in sizes:
+            lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=base[lg]["rs_level0"])
+    return out
+
+
 def bench_families(lrcc, torch, dev, stream, m=8_000_000):
     """The paper's component families (Sec. 4): collections of random lists, random
     trees of degree k and random graphs of edge density d, all with m edges; hook
@@ -654,9 +693,11 @@ def main():
                               "sample": "the same random-layout list as the oracle leg", "seconds": tp}
 
     batched = serving = None
-    families = None
+    families = sweep = None
     if rank == 0 and not args.no_families:
         families = bench_families(lrcc, torch, dev, stream)
+        sweep = bench_lr_sweep(lrcc, torch, dev, stream, (16, 18, 20, 22, 24, 26, 28) if args.workload == "large"
+                               else (12, 14, 16, 18, 20))
     if rank == 0 and not args.no_batched:
         del rank_out, label, src, dst, succ
         torch.cuda.empty_cache()
@@ -685,7 +726,7 @@ def main():
                        "problem_bytes_frac": (8 * m_cc + 4 * n_cc) / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
                        "rounds": cc_stats["rounds"]},
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
-                "batched": batched, "serving": serving, "cc_families": families,
+                "batched": batched, "serving": serving, "cc_families": families, "lr_sweep": sweep,
                 **extra}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -257,6 +257,8 @@ typedef struct lrcc_plan {
  * in [log2_lo, log2_hi] get `plan`. */
 lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* plan);
 lrcc_status lrcc_get_plan(int kind, int64_t n, lrcc_plan* out);
+/* Restores the built-in plan table (undoing every lrcc_set_plan). */
+lrcc_status lrcc_reset_plans(void);
 
 /*
  * Phase timing. While enabled (process-wide), list-ranking calls launch their

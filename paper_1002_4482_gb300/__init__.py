@@ -32,7 +32,7 @@ KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
            "lr_rank_host", "cc_label_host", "lr_scan", "lr_scan_forest",
            "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "cc_label_batched_sized", "lrcc_last_status", "lrcc_last_stats",
-           "lrcc_set_plan", "lrcc_get_plan", "lrcc_release", "lrcc_workspace_bytes",
+           "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity")
 
@@ -106,7 +106,7 @@ def load() -> ctypes.CDLL:
                   "lr_rank_batched",
                   "lr_rank_batched_sized",
                   "cc_label_batched", "cc_label_batched_sized",
-                  "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan",
+                  "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
             getattr(lib, f).restype = i
         _lib = lib
@@ -326,6 +326,11 @@ def last_stats(stream=None) -> dict:
 def set_plan(kind: int, log2_lo: int = 0, log2_hi: int = 32, **fields) -> None:
     p = Plan(**fields)
     _call(load().lrcc_set_plan(kind, log2_lo, log2_hi, ctypes.byref(p)), "lrcc_set_plan")
+
+
+def reset_plans() -> None:
+    """Restore the built-in plan table."""
+    _call(load().lrcc_reset_plans(), "lrcc_reset_plans")
 
 
 def get_plan(kind: int, n: int) -> dict:

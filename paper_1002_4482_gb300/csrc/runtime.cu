@@ -36,7 +36,8 @@ int log2_ceil(int64_t n) {
 }
 
 // Built-in plans: the choices of an autotune run on a GB300
-// (python -m paper_1002_4482_gb300.autotune), per size class of ceil(log2 n).
+// (python -m paper_1002_4482_gb300.autotune), per size class of ceil(log2 n),
+// with the first level of 2^23..2^28 from a sweep of every size in that range.
 void init_plans_locked() {
     if (g_plan_init) return;
     for (int k = 0; k < 6; ++k)
@@ -48,10 +49,13 @@ void init_plans_locked() {
                 p.rs_level0 = 1, p.rs_spacing0 = 8, p.rs_spacing = 16;
             } else if (l <= 22) {
                 p.rs_level0 = 1, p.rs_spacing0 = 8, p.rs_spacing = 8;
-            } else if (l <= 26) {
+            } else if (l <= 24) {
                 p.rs_level0 = 1, p.rs_spacing0 = 16, p.rs_spacing = 8;
+            } else if (l <= 27) {
+                // the read-only first level pays off once the list outgrows L2
+                // (8-byte walk words of 2^25 elements are 256 MB)
+                p.rs_level0 = 2, p.rs_spacing0 = 16, p.rs_spacing = 8;
             } else {
-                // the read-only first level pays off once the list is far beyond L2
                 p.rs_level0 = 2, p.rs_spacing0 = 32, p.rs_spacing = 8;
             }
             // batched lists: minimum spacing of the in-block ruling sets
@@ -613,6 +617,13 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
         if (plan->seed) p.seed = plan->seed;
         if (plan->cc_sample) p.cc_sample = plan->cc_sample;
     }
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_reset_plans(void) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plan_init = false;
+    init_plans_locked();
     return LRCC_OK;
 }
 

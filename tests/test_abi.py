@@ -110,6 +110,15 @@ def test_plan_table_roundtrip(lib):
         lrcc.set_plan(lrcc.KIND_CC, 20, 20, cc_hook=before)
 
 
+def test_reset_plans_restores_the_builtin_table(lib):
+    lrcc.reset_plans()
+    before = {k: lrcc.get_plan(k, 1 << 24) for k in (lrcc.KIND_LR, lrcc.KIND_CC, lrcc.KIND_LR_BATCH)}
+    lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_spacing0=128, rs_level0=2, seed=7)
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=4, cc_sample=3)
+    lrcc.reset_plans()
+    assert {k: lrcc.get_plan(k, 1 << 24) for k in before} == before
+
+
 def test_workspace_query(lib):
     L = lrcc.load()
     assert L.lrcc_workspace_query(lrcc.KIND_LR, 1000, 0) == 0          # one block, no workspace

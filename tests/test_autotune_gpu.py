@@ -37,9 +37,4 @@ def test_quick_tune_installs_checked_plans(tmp_path):
 
 
 def _restore_builtin_plans():
-    # the library's built-in table (see csrc/runtime.cu)
-    for lo, hi, l0, d0, d in ((0, 18, 1, 8, 16), (19, 22, 1, 8, 8), (23, 26, 1, 16, 8), (27, 32, 2, 32, 8)):
-        lrcc.set_plan(lrcc.KIND_LR, lo, hi, rs_level0=l0, rs_spacing0=d0, rs_spacing=d, rs_small=16384, rs_chains=1)
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=1)
-    lrcc.set_plan(lrcc.KIND_LR_BATCH, 0, 32, rs_spacing0=64)
-    lrcc.set_plan(lrcc.KIND_CC_BATCH, 0, 32, cc_hook=1)
+    lrcc.reset_plans()

@@ -82,8 +82,7 @@ def level0(request):
 
 def _restore_level0():
     # the library's built-in table (see csrc/runtime.cu)
-    for lo, hi, l0, d0, d in ((0, 18, 1, 8, 16), (19, 22, 1, 8, 8), (23, 26, 1, 16, 8), (27, 32, 2, 32, 8)):
-        lrcc.set_plan(lrcc.KIND_LR, lo, hi, rs_level0=l0, rs_spacing0=d0, rs_spacing=d, rs_small=16384, rs_chains=1)
+    lrcc.reset_plans()
 
 
 def test_without_graphs_and_repeated():

@@ -76,15 +76,12 @@ def test_scan_under_every_first_level_plan():
     succ, head = gen.list_random(400_000, 75)
     val = np.random.default_rng(5).integers(0, 50, len(succ)).astype(np.int32)
     expect = oracle.lr_scan(succ, val, head)
-    base = lrcc.get_plan(lrcc.KIND_LR, 400_000)
     try:
         for l0, d0 in ((1, 8), (2, 32), (1, 256), (2, 4)):
             lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=l0, rs_spacing0=d0)
             assert np.array_equal(_scan(succ, val, head), expect), (l0, d0)
     finally:
-        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=base["rs_level0"], rs_spacing0=base["rs_spacing0"])
-        for lo, hi, l0, d0, d in ((0, 18, 1, 8, 16), (19, 22, 1, 8, 8), (23, 26, 1, 16, 8), (27, 32, 2, 32, 8)):
-            lrcc.set_plan(lrcc.KIND_LR, lo, hi, rs_level0=l0, rs_spacing0=d0, rs_spacing=d)
+        lrcc.reset_plans()
 
 
 @pytest.mark.parametrize("n", [7, 20_000, 300_000])

@@ -118,10 +118,13 @@ lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t 
  * Weighted list ranking of a forest of lists: succ holds any number of
  * disjoint lists covering all n elements (tails -1 or self-loops; no head is
  * given), and out[i] is the sum of val from i to the tail of i's own list,
- * modulo 2^32. Computed by pointer jumping over all lists at once (Sec. 3.1,
- * ceil(log2 n) rounds, O(n log n) work). An element named by two successors,
- * a cycle or a successor out of range records LRCC_ERR_INVALID_INPUT.
- * Workspace: 16 bytes per element plus one bit.
+ * modulo 2^32. The heads (elements no successor names) become extra splitters
+ * of the ruling set's first level, and the much smaller forest of splitters is
+ * summed by pointer jumping (Sec. 3.1). When a value is negative or the values
+ * total 2^31 or more, the whole forest is summed by pointer jumping instead
+ * (O(n log n) work, any values). An element named by two successors, a cycle
+ * or a successor out of range records LRCC_ERR_INVALID_INPUT. Workspace: about
+ * 36 bytes per element (the first level is sized for every element a head).
  */
 lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, int32_t* out, void* stream);
 

@@ -30,7 +30,8 @@ struct DevCtl {
     int seg_next;        // batched union path: next edge slice of the current pass
     int seg_next_v;      // batched union path: next vertex slice of the current shortcut
     int scan_bad;        // weighted ranks: the values are outside the supported range; skip the work
-    int pad[2];
+    int ff_extra;        // forest ranks: list heads that became extra first-level splitters
+    int pad[1];
     unsigned long long scan_total;   // weighted ranks: sum of the values
 };
 

@@ -115,10 +115,11 @@ int persistent_grid(Ctx* c, const void* kernel, int block, size_t smem = 0);
 // needs the in-place first level (L.readonly false).
 lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
                           int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val = nullptr);
-// Weighted ranks of a forest of lists by pointer jumping; workspace lr_scan_forest_ws(n).
-size_t lr_scan_forest_ws(int64_t n);
+// Weighted ranks of a forest of lists (ruling set with the heads as extra
+// splitters; pointer jumping when the values rule that out).
+size_t lr_scan_forest_ws(int64_t n, const Plan& p);
 lrcc_status lr_enqueue_scan_forest(Ctx* c, cudaStream_t s, const int32_t* succ, const int32_t* val, int64_t n,
-                                   int32_t* out);
+                                   int32_t* out, const Plan& p);
 lrcc_status lr_enqueue_wyllie(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
                               int32_t* rank, const Plan& p);
 size_t lr_wyllie_ws(int64_t n, const Plan& p);

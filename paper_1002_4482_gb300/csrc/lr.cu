@@ -209,8 +209,10 @@ __global__ void __launch_bounds__(BLOCK)
 template <int K>
 __global__ void __launch_bounds__(BLOCK)
     rs_walk(uint64_t* __restrict__ W, const int32_t* __restrict__ snext, const int32_t* __restrict__ sw,
-            uint64_t* __restrict__ Rout, int r, int* work, int64_t nlevel, DevCtl* ctl) {
+            uint64_t* __restrict__ Rout, int r, int* work, int64_t nlevel, DevCtl* ctl,
+            const int* r_extra = nullptr) {
     if (ctl->scan_bad) return;
+    if (r_extra) r += *r_extra;   // splitters added on the device (forest heads)
     constexpr int CHUNK = 64;
     const int lane = threadIdx.x & 31;
     int pool = 0, pool_end = 0;
@@ -993,31 +995,108 @@ __global__ void rs_scan_verdict(DevCtl* ctl) {
 
 // ------------------------------------------- weighted ranks of a forest
 
-// A forest of lists has no single head, so its weighted ranks are taken by
-// pointer jumping (Sec. 3.1) over every list at once: words (next or NIL,
-// value), ceil(log2 n) rounds of (next, value) <- (next[next], value +
-// value[next]). The pack pass also checks that no element is named by two
-// successors (one bit per element, set with atomicOr in a bitmap L2 holds);
-// an element still linked after the last round lies on a cycle.
+// A forest of lists has no single head. Its weighted ranks take the ruling
+// set with every list head as an extra first-level splitter (the heads are the
+// elements no successor names, found with one bit per element in a bitmap L2
+// holds, which also catches an element named twice); the first level walks
+// as for one list, and the splitters, a much smaller forest, are summed by
+// pointer jumping (Sec. 3.1): words (next or NIL, value), rounds of (next,
+// value) <- (next[next], value + value[next]); a splitter still linked after
+// the last round lies on a cycle. When the values rule out the 31-bit fields
+// of the first level (a negative value, or a total of 2^31 or more), the
+// whole forest is summed by pointer jumping instead (fs_pack).
+__global__ void __launch_bounds__(BLOCK)
+    ff_indeg(const int32_t* __restrict__ succ, int64_t n, uint32_t* has_pred, DevCtl* ctl) {
+    const uint64_t pol = policy_evict_first();
+    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+        const int32_t sx = ld_stream(succ + i, pol);
+        const bool tail = (sx == -1) | (sx == i);
+        if (tail) continue;
+        if (sx < 0 || sx >= n) {
+            record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+            continue;
+        }
+        const uint32_t bit = 1u << (sx & 31);
+        if (atomicOr(has_pred + (sx >> 5), bit) & bit) record_error(ctl, LRCC_ERR_INVALID_INPUT, sx);
+    }
+}
+
+// Forest first level: the stratified splitter of every block of D ids keeps
+// its block number as index; every other head takes an index from nb on (one
+// counter atomic per warp). Walk words as in rs_select0, with the value as
+// weight.
+__global__ void __launch_bounds__(BLOCK)
+    ff_select0(const int32_t* __restrict__ succ, const int32_t* __restrict__ val, int64_t n,
+               const uint32_t* __restrict__ has_pred, uint64_t* __restrict__ W, int32_t* __restrict__ snext,
+               int32_t* __restrict__ sw, int logD, int64_t nb, int64_t r1_max, uint32_t seed, DevCtl* ctl) {
+    if (ctl->scan_bad) return;
+    const uint64_t pol = policy_evict_first();
+    const int64_t D = int64_t(1) << logD;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform trip count for the ballot
+    for (int64_t base = (int64_t)blockIdx.x * BLOCK + (threadIdx.x & ~31); base < n; base += (int64_t)gridDim.x * BLOCK) {
+        const int64_t i = base + lane;
+        const bool in = i < n;
+        int32_t sx = -1, v = 0;
+        if (in) {
+            sx = ld_stream(succ + i, pol);
+            v = ld_stream(val + i, pol);
+        }
+        const bool tail = (sx == -1) | (sx == i);
+        const uint32_t nx = (tail || sx < 0 || sx >= n) ? NIL : (uint32_t)sx;
+        const int64_t b = i >> logD;
+        const uint32_t size = in ? (uint32_t)min(D, n - (b << logD)) : 1u;
+        const bool strat = in && (uint32_t)(i - (b << logD)) == block_offset((uint32_t)b, size, seed);
+        const bool head = in && !((has_pred[i >> 5] >> (i & 31)) & 1u);
+        const bool extra = head && !strat;
+        const unsigned m = __ballot_sync(0xffffffffu, extra);
+        int first = 0;
+        if (lane == 0 && m) first = atomicAdd(&ctl->ff_extra, __popc(m));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (!in) continue;
+        int64_t j = -1;
+        if (strat) j = b;
+        else if (extra) j = nb + first + __popc(m & lanemask_lt());
+        if (j >= r1_max) {
+            record_error(ctl, LRCC_ERR_INVALID_INPUT, -7);
+            j = -1;
+        }
+        if (j >= 0) {
+            W[i] = pack(nx | SPL, (uint32_t)j);
+            snext[j] = (int32_t)nx;
+            sw[j] = v;
+        } else {
+            W[i] = pack(nx, (uint32_t)v);
+        }
+    }
+}
+
+// Verdict for the forest: values outside the first level's range select the
+// pointer-jumping form (no error; that form takes any values).
+__global__ void ff_verdict(DevCtl* ctl) {
+    if (ctl->scan_bad || ctl->scan_total >= (1ull << 31)) ctl->scan_bad = 1;
+}
+
 __global__ void __launch_bounds__(BLOCK)
     fs_pack(const int32_t* __restrict__ succ, const int32_t* __restrict__ val, int64_t n, uint64_t* __restrict__ W,
             uint32_t* named, DevCtl* ctl) {
+    if (!ctl->scan_bad) return;   // only when the ruling-set form cannot take the values
     const uint64_t pol = policy_evict_first();
     for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
         const int32_t sx = ld_stream(succ + i, pol);
         const bool tail = (sx == -1) | (sx == i);
         const bool bad = !tail && (sx < 0 || sx >= n);
-        if (bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
-        if (!tail && !bad) {
-            const uint32_t bit = 1u << (sx & 31);
-            if (atomicOr(named + (sx >> 5), bit) & bit) record_error(ctl, LRCC_ERR_INVALID_INPUT, sx);
-        }
         W[i] = pack((tail || bad) ? NIL : (uint32_t)sx, (uint32_t)ld_stream(val + i, pol));
     }
 }
 
 __global__ void __launch_bounds__(BLOCK)
-    fs_jump(const uint64_t* __restrict__ Win, uint64_t* __restrict__ Wout, int64_t n) {
+    fs_jump(const uint64_t* __restrict__ Win, uint64_t* __restrict__ Wout, int64_t n, const int* extra,
+            const DevCtl* ctl) {
+    // two uses: the whole forest when the values rule out the ruling set
+    // (extra == nullptr), or the forest of first-level splitters (n + *extra of them)
+    if (extra ? ctl->scan_bad : !ctl->scan_bad) return;
+    if (extra) n += *extra;
     for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
         uint64_t w = Win[i];
         const uint32_t nx = lo32(w);
@@ -1030,7 +1109,9 @@ __global__ void __launch_bounds__(BLOCK)
 }
 
 __global__ void __launch_bounds__(BLOCK)
-    fs_final(const uint64_t* __restrict__ W, int64_t n, int32_t* __restrict__ out, DevCtl* ctl) {
+    fs_final(const uint64_t* __restrict__ W, int64_t n, int32_t* __restrict__ out, const int* extra, DevCtl* ctl) {
+    if (extra ? ctl->scan_bad : !ctl->scan_bad) return;
+    if (extra) n += *extra;
     for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
         const uint64_t w = W[i];
         if (lo32(w) != NIL) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
@@ -1282,34 +1363,112 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     return cuda_status(cudaGetLastError());
 }
 
-size_t lr_scan_forest_ws(int64_t n) {
-    return 2 * align_up(sizeof(uint64_t) * (size_t)n, 256) + align_up(sizeof(uint32_t) * (size_t)((n + 31) / 32), 256);
+// Forest layout: walk words W0 (8 B per element), the has-predecessor bitmap,
+// then for r1_max = nb + n first-level splitters (every element could be a
+// head) their successor and weight, two word buffers and the sums. The
+// pointer-jumping form reuses W0 and the first word buffer.
+struct ForestLayout {
+    int logD;
+    int64_t nb, r1_max;
+    size_t off_W0, off_pred, off_snext, off_sw, off_R1, off_R1b, off_S1, bytes;
+};
+
+ForestLayout forest_layout(int64_t n, int spacing0) {
+    ForestLayout F;
+    F.logD = 2;
+    while (F.logD < 20 && (int64_t(1) << (F.logD + 1)) <= spacing0) ++F.logD;
+    F.nb = (n + (int64_t(1) << F.logD) - 1) >> F.logD;
+    F.r1_max = F.nb + n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    F.off_W0 = take(sizeof(uint64_t) * (size_t)n);
+    F.off_pred = take(sizeof(uint32_t) * (size_t)((n + 31) / 32));
+    F.off_snext = take(sizeof(int32_t) * (size_t)F.r1_max);
+    F.off_sw = take(sizeof(int32_t) * (size_t)F.r1_max);
+    F.off_R1 = take(sizeof(uint64_t) * (size_t)F.r1_max);
+    F.off_R1b = take(sizeof(uint64_t) * (size_t)F.r1_max);
+    F.off_S1 = take(sizeof(int32_t) * (size_t)F.r1_max);
+    F.bytes = off;
+    return F;
 }
 
+size_t lr_scan_forest_ws(int64_t n, const Plan& p) { return forest_layout(n, p.rs_spacing0).bytes; }
+
 lrcc_status lr_enqueue_scan_forest(Ctx* c, cudaStream_t s, const int32_t* succ, const int32_t* val, int64_t n,
-                                   int32_t* out) {
+                                   int32_t* out, const Plan& p) {
+    const ForestLayout F = forest_layout(n, p.rs_spacing0);
     char* base = static_cast<char*>(c->ws);
-    uint64_t* W0 = reinterpret_cast<uint64_t*>(base);
-    uint64_t* W1 = reinterpret_cast<uint64_t*>(base + align_up(sizeof(uint64_t) * (size_t)n, 256));
-    uint32_t* named = reinterpret_cast<uint32_t*>(base + 2 * align_up(sizeof(uint64_t) * (size_t)n, 256));
-    const int g = stream_grid(c, n, (const void*)fs_jump);
-    cudaMemsetAsync(named, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
+    uint64_t* W0 = reinterpret_cast<uint64_t*>(base + F.off_W0);
+    uint32_t* pred = reinterpret_cast<uint32_t*>(base + F.off_pred);
+    int32_t* snext = reinterpret_cast<int32_t*>(base + F.off_snext);
+    int32_t* sw = reinterpret_cast<int32_t*>(base + F.off_sw);
+    uint64_t* R1 = reinterpret_cast<uint64_t*>(base + F.off_R1);
+    uint64_t* R1b = reinterpret_cast<uint64_t*>(base + F.off_R1b);
+    int32_t* S1 = reinterpret_cast<int32_t*>(base + F.off_S1);
+    DevCtl* ctl = c->ctl;
+    const int g = stream_grid(c, n, (const void*)ff_indeg);
+    const uint32_t seed = (uint32_t)(p.seed ^ (p.seed >> 32));
+    cudaMemsetAsync(pred, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
     phase_begin(c, s);
-    fs_pack<<<g, BLOCK, 0, s>>>(succ, val, n, W0, named, c->ctl);
-    phase_end(c, s, PH_WY_PACK);
+    ff_indeg<<<g, BLOCK, 0, s>>>(succ, n, pred, ctl);
+    rs_scan_check<<<g, BLOCK, 0, s>>>(val, n, ctl);
+    ff_verdict<<<1, 1, 0, s>>>(ctl);
+    ff_select0<<<g, BLOCK, 0, s>>>(succ, val, n, pred, W0, snext, sw, F.logD, F.nb, F.r1_max, seed, ctl);
+    phase_end(c, s, PH_SELECT0);
+    phase_begin(c, s);
+    {
+        const int gw = persistent_grid(c, (const void*)rs_walk<1>, BLOCK);
+        rs_walk<1><<<gw, BLOCK, 0, s>>>(W0, snext, sw, R1, (int)F.nb, &ctl->work[0], n, ctl, &ctl->ff_extra);
+    }
+    phase_end(c, s, PH_WALK0);
+    // the splitter forest by pointer jumping; rounds for the largest possible count
     int rounds = 0;
-    while ((int64_t(1) << rounds) < n) ++rounds;
-    uint64_t* a = W0;
-    uint64_t* b = W1;
+    while ((int64_t(1) << rounds) < F.r1_max) ++rounds;
+    const int g1 = stream_grid(c, F.nb, (const void*)fs_jump);
+    uint64_t* a = R1;
+    uint64_t* b = R1b;
     for (int r = 0; r < rounds; ++r) {
         phase_begin(c, s);
-        fs_jump<<<g, BLOCK, 0, s>>>(a, b, n);
+        fs_jump<<<g1, BLOCK, 0, s>>>(a, b, F.nb, &ctl->ff_extra, ctl);
         phase_end(c, s, PH_WY_JUMP);
         std::swap(a, b);
     }
     phase_begin(c, s);
-    fs_final<<<g, BLOCK, 0, s>>>(a, n, out, c->ctl);
-    phase_end(c, s, PH_WY_FINAL);
+    fs_final<<<g1, BLOCK, 0, s>>>(a, F.nb, S1, &ctl->ff_extra, ctl);
+    phase_end(c, s, PH_FINAL);
+    {
+        const bool v = aligned16(out);
+        const void* k = v ? (const void*)rs_expand0<true> : (const void*)rs_expand0<false>;
+        const int ge = stream_grid(c, (n + 3) / 4, k);
+        phase_begin(c, s);
+        if (v) rs_expand0<true><<<ge, BLOCK, 0, s>>>(W0, n, S1, F.r1_max, out, 0, ctl);
+        else rs_expand0<false><<<ge, BLOCK, 0, s>>>(W0, n, S1, F.r1_max, out, 0, ctl);
+        phase_end(c, s, PH_EXPAND0);
+    }
+    // values out of the first level's range: the whole forest by pointer jumping
+    // (these kernels return at once otherwise)
+    {
+        uint64_t* x = W0;
+        uint64_t* y = R1;   // r1_max >= n words
+        phase_begin(c, s);
+        fs_pack<<<g, BLOCK, 0, s>>>(succ, val, n, x, pred, ctl);
+        phase_end(c, s, PH_WY_PACK);
+        int rr = 0;
+        while ((int64_t(1) << rr) < n) ++rr;
+        for (int r = 0; r < rr; ++r) {
+            phase_begin(c, s);
+            fs_jump<<<g, BLOCK, 0, s>>>(x, y, n, nullptr, ctl);
+            phase_end(c, s, PH_WY_JUMP);
+            std::swap(x, y);
+        }
+        phase_begin(c, s);
+        fs_final<<<g, BLOCK, 0, s>>>(x, n, out, nullptr, ctl);
+        phase_end(c, s, PH_WY_FINAL);
+    }
     return cuda_status(cudaGetLastError());
 }
 

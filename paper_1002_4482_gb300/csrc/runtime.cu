@@ -400,13 +400,13 @@ lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, i
     lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
-    const Plan p = plan_for(KIND_LR_WYLLIE, n);
-    st = ensure_ws(c, lr_scan_forest_ws(n));
+    const Plan p = plan_for(KIND_LR, n);
+    st = ensure_ws(c, lr_scan_forest_ws(n, p));
     if (st != LRCC_OK) return st;
     const std::vector<uint64_t> key = {7, (uint64_t)succ, (uint64_t)val, (uint64_t)n, (uint64_t)out};
     st = launch_recorded(c, p, key, [&](cudaStream_t s) {
         reset_ctl(c, s);
-        return lr_enqueue_scan_forest(c, s, succ, val, n, out);
+        return lr_enqueue_scan_forest(c, s, succ, val, n, out, p);
     });
     c->last_kind = 7;
     c->last_levels = 0;

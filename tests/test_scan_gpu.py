@@ -132,6 +132,18 @@ def test_forest_sums_wrap_modulo_2_32():
     assert np.array_equal(_forest(succ, val), oracle.lr_scan_forest(succ, val))
 
 
+def test_forest_large_totals_take_the_pointer_jumping_form():
+    # non-negative values whose total passes 2^31: the first level's 31-bit fields cannot
+    # hold the sums, so the whole forest is summed by pointer jumping (no error)
+    n = 300_000
+    perm = gen.permutation(n, 82)
+    succ = np.full(n, -1, np.int32)
+    for piece in np.array_split(perm, 7):
+        succ[piece[:-1]] = piece[1:]
+    val = np.full(n, 2**31 // n + 100, np.int32)
+    assert np.array_equal(_forest(succ, val), oracle.lr_scan_forest(succ, val))
+
+
 @pytest.mark.parametrize("case", ["named_twice", "cycle", "out_of_range"])
 def test_forest_invalid_inputs_are_reported(case):
     n = 10_000

@@ -21,7 +21,11 @@
 // larger root was linked meanwhile, keep joining (old parent, smaller root)
 // until one link lands, so each pass joins every edge and the next pass only
 // confirms; 3 = rule 1 in the first pass, rule 2 after it. All give the same
-// labels.
+// labels. Rule 4, the paper's own round structure, is in cc_sv.cu.
+//
+// Before the loop, an optional sample pass (plan.cc_sample) hooks and
+// shortcuts a prefix of the edge list, which forms most of a large component
+// for a fraction of a pass (see cc_run).
 #include <algorithm>
 
 #include "cc_device.cuh"
@@ -55,12 +59,13 @@ __global__ void __launch_bounds__(BLOCK) cc_init(int32_t* __restrict__ parent, i
 // mode 3: single hooks in the first pass (cheap while every tree is a
 // singleton), relink afterwards.
 //
-// Edges of a pass come from the input (first passes) or from an active-edge
-// buffer: from the second pass on, an edge whose endpoints already share a
-// parent (after the previous shortcut, a root) can never join two trees
-// again, because trees only merge; the others are appended, one warp-wide
-// atomic per 128 edges, to the buffer the next pass reads. In the first pass
-// every parent is still the vertex itself, so the parents are not read.
+// Edges of a pass come from the input or from an active-edge buffer: from
+// the first pass after a shortcut on (the sample pass counts as a round), an
+// edge whose endpoints already share a parent (after the shortcut, a root)
+// can never join two trees again, because trees only merge; the others are
+// staged per warp in shared memory and appended in batches to the buffer the
+// next pass reads. The first pass of all (every parent still the vertex
+// itself) appends nothing: every edge would be kept.
 struct ActiveEdges {
     int2* buf[2];      // active buffers 1 and 2 (edge = (u, v))
     int64_t cap;       // edges each buffer holds; 0 = no compaction

@@ -53,7 +53,22 @@ struct RsLayout {
         off_vis = 0;
     size_t bytes = 0;
 };
-RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid);
+// extra1: extra first-level splitters (the heads of batched lists ranked as one list)
+RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1 = 0);
+
+// Batched lists ranked as one list by the read-only first level: K lists own
+// [off[k], off[k+1]) of succ with local ids; device scratch for the global
+// successors, each list's head splitter, the extra splitters' elements and the
+// first list's global head.
+struct BatchUnion {
+    const int64_t* off = nullptr;
+    const int32_t* heads = nullptr;
+    int64_t K = 0;
+    int32_t* gsucc = nullptr;
+    int32_t* head_spl = nullptr;
+    int32_t* extra_elem = nullptr;
+    int64_t* head_dev = nullptr;
+};
 int rs_walk_grid(Ctx* c, const Plan& p);
 
 // Phase ids for timing mode (names in runtime.cu).
@@ -114,7 +129,8 @@ int persistent_grid(Ctx* c, const void* kernel, int block, size_t smem = 0);
 // val != nullptr: inclusive weighted suffix sums (modulo 2^32) instead of ranks;
 // needs the in-place first level (L.readonly false).
 lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
-                          int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val = nullptr);
+                          int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val = nullptr,
+                          const BatchUnion* U = nullptr);
 // Weighted ranks of a forest of lists (ruling set with the heads as extra
 // splitters; pointer jumping when the values rule that out).
 size_t lr_scan_forest_ws(int64_t n, const Plan& p);
@@ -141,6 +157,12 @@ lrcc_status lr_batched_run(Ctx* c, const int32_t* succ, const int64_t* off, cons
 lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const int64_t* eoff,
                            const int64_t* voff, int64_t count, int64_t total_edges, int32_t* label, const Plan& p);
 size_t lr_batched_ws(int64_t total_nodes, int64_t count);
+// Batched lists of at least 2^22 elements in all whose batched plan (looked up
+// by the total) has the read-only first level are ranked together as one list.
+bool batch_union_applies(int64_t total, const Plan& batch_plan);
+size_t lr_batched_union_ws(Ctx* c, int64_t total, int64_t K);
+lrcc_status lr_batched_union(Ctx* c, cudaStream_t s, const int32_t* succ, const int64_t* off, const int32_t* heads,
+                             int64_t K, int64_t total, int32_t* rank);
 size_t cc_batched_ws(int64_t count, int64_t total_edges);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

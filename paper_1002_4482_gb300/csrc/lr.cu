@@ -323,6 +323,12 @@ struct Level0 {
     int logD;
     uint32_t head_off;   // offset of the head inside its block
     uint32_t seed;
+    // batched lists ranked as one list (see lr_enqueue_rs): the first list's
+    // head, read on the device (bh and head_off are derived from it), and the
+    // heads of the other lists that are extra splitters nb, nb + 1, ...
+    const int64_t* head_dev = nullptr;
+    const int32_t* extra = nullptr;
+    const int* extra_count = nullptr;
 };
 
 struct Chunks {
@@ -353,6 +359,7 @@ __device__ __forceinline__ int64_t splitter_index0(int64_t x, const Level0& L0) 
 
 // Element of splitter j.
 __device__ __forceinline__ int64_t splitter_node0(int64_t j, const Level0& L0) {
+    if (j >= L0.nb) return L0.extra[j - L0.nb];
     const int64_t D = int64_t(1) << L0.logD;
     int64_t b = j + L0.bh;
     if (b >= L0.nb) b -= L0.nb;
@@ -368,13 +375,18 @@ template <int K>
 __global__ void __launch_bounds__(BLOCK)
     rs_walk0c(const int32_t* __restrict__ succ, Level0 L0, Chunks C, uint64_t* __restrict__ R1, int* work,
               DevCtl* ctl) {
+    if (L0.head_dev) {
+        const int64_t gh = *L0.head_dev;
+        L0.bh = gh >> L0.logD;
+        L0.head_off = (uint32_t)(gh - (L0.bh << L0.logD));
+    }
     constexpr int WCHUNK = 64;
     __shared__ int s_fill;
     __shared__ int s_cnt[NSEG][NBK];
     for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) (&s_cnt[0][0])[t] = 0;
     if (threadIdx.x == 0) s_fill = 0;
     __syncthreads();
-    const int64_t r = L0.nb;
+    const int64_t r = L0.nb + (L0.extra_count ? *L0.extra_count : 0);
     const int lane = threadIdx.x & 31;
     int pool = 0, pool_end = 0;
     bool exhausted = false;
@@ -963,6 +975,184 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+// ------------------------------------------------ batched lists as one list
+//
+// Lists k = 0..K-1 own elements [off[k], off[k+1]) with local ids. They are
+// ranked as one list by the read-only first level: every element gets a
+// global successor (off[k] + local, or -1 at a tail); the first non-empty
+// list's head is the head; the head of every other list is a first-level
+// splitter (its block's stratified splitter, or an extra splitter nb + e when
+// that is another element); after the walk, the splitter that ends list k is
+// linked to the head splitter of the next non-empty list, and the unused extra
+// slots become a tail of empty splitters. Ranks along that one list are the
+// local ranks plus the number of elements of the later lists, which a last
+// pass subtracts. A walk never steps onto a head (nothing names it), so the
+// walk recognises splitters by their hash as for one list.
+
+// The list that holds element i (for empty lists, the last list starting at i).
+__device__ __forceinline__ int64_t find_list(const int64_t* __restrict__ off, int64_t K, int64_t i) {
+    int64_t lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int BL_TILE = BLOCK * 16;
+
+// Global successors; one binary search per tile of elements.
+__global__ void __launch_bounds__(BLOCK)
+    bl_gsucc(const int32_t* __restrict__ succ, const int64_t* __restrict__ off, int64_t K, int64_t n,
+             int32_t* __restrict__ gsucc, DevCtl* ctl) {
+    __shared__ int64_t s_k;
+    for (int64_t t0 = (int64_t)blockIdx.x * BL_TILE; t0 < n; t0 += (int64_t)gridDim.x * BL_TILE) {
+        if (threadIdx.x == 0) s_k = find_list(off, K, t0);
+        __syncthreads();
+        int64_t k = s_k;
+        __syncthreads();
+        for (int64_t i = t0 + threadIdx.x; i < min(t0 + BL_TILE, n); i += BLOCK) {
+            while (k + 1 < K && off[k + 1] <= i) ++k;
+            const int64_t base = off[k], len = off[k + 1] - base;
+            const int32_t sx = succ[i];
+            int32_t g = -1;
+            if (sx != -1 && sx != i - base) {
+                if (sx < 0 || sx >= len) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+                else g = (int32_t)(base + sx);
+            }
+            gsucc[i] = g;
+        }
+    }
+}
+
+// One block: the first list's head, and the head splitter of every list.
+__global__ void __launch_bounds__(1024)
+    bl_heads(const int64_t* __restrict__ off, const int32_t* __restrict__ heads, int64_t K, int64_t n, int logD,
+             int64_t nb, uint32_t seed, int32_t* __restrict__ head_spl, int32_t* __restrict__ extra_elem,
+             int64_t* head_dev, DevCtl* ctl) {
+    __shared__ int64_t s_first;
+    __shared__ int s_warp[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) {
+        int64_t k0 = 0;
+        while (k0 < K && off[k0 + 1] == off[k0]) ++k0;
+        s_first = k0;
+        int64_t gh = 0;
+        if (k0 < K) {
+            const int64_t len = off[k0 + 1] - off[k0];
+            if (heads[k0] < 0 || heads[k0] >= len) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)k0);
+            else gh = off[k0] + heads[k0];
+        }
+        *head_dev = gh;
+    }
+    __syncthreads();
+    const int64_t k0 = s_first;
+    const int64_t gh0 = *head_dev;
+    const int64_t D = int64_t(1) << logD;
+    const int64_t bh = gh0 >> logD;
+    const int64_t per = (K + 1023) / 1024;
+    const int64_t kb = min(K, (int64_t)t * per), ke = min(K, kb + per);
+    // a list's head and whether it is its block's stratified splitter
+    auto head_of = [&](int64_t k, int64_t* gh, bool* strat) {
+        const int64_t len = off[k + 1] - off[k];
+        int64_t h = off[k];
+        if (heads[k] < 0 || heads[k] >= len) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)k);
+        else h = off[k] + heads[k];
+        const int64_t b = h >> logD;
+        const uint32_t size = (uint32_t)min(D, n - (b << logD));
+        *gh = h;
+        *strat = b != bh && (uint32_t)(h - (b << logD)) == block_offset((uint32_t)b, size, seed);
+    };
+    int cnt = 0;
+    for (int64_t k = kb; k < ke; ++k) {
+        if (k == k0 || off[k + 1] == off[k]) continue;
+        int64_t gh;
+        bool strat;
+        head_of(k, &gh, &strat);
+        cnt += !strat;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < 32; ++w) {
+        before += w < wid ? s_warp[w] : 0;
+        total += s_warp[w];
+    }
+    int e = before + incl - cnt;
+    for (int64_t k = kb; k < ke; ++k) {
+        if (off[k + 1] == off[k]) {
+            head_spl[k] = -1;
+            continue;
+        }
+        if (k == k0) {
+            head_spl[k] = 0;
+            continue;
+        }
+        int64_t gh;
+        bool strat;
+        head_of(k, &gh, &strat);
+        if (strat) {
+            const int64_t b = gh >> logD;
+            head_spl[k] = (int32_t)(b >= bh ? b - bh : b - bh + nb);
+        } else {
+            head_spl[k] = (int32_t)(nb + e);
+            extra_elem[e] = (int32_t)gh;
+            ++e;
+        }
+    }
+    if (t == 0) ctl->ff_extra = total;
+}
+
+// After the first-level walk: the splitter that ends list k (its word names no
+// next splitter) is linked to the next non-empty list's head splitter; the
+// unused extra slots become a chain of empty splitters after the last list.
+__global__ void __launch_bounds__(BLOCK)
+    bl_link(uint64_t* __restrict__ R1, int64_t r1_max, const int64_t* __restrict__ off, int64_t K,
+            const int32_t* __restrict__ head_spl, Level0 L0, DevCtl* ctl) {
+    const int64_t gh = *L0.head_dev;
+    L0.bh = gh >> L0.logD;
+    L0.head_off = (uint32_t)(gh - (L0.bh << L0.logD));
+    const int64_t r_real = L0.nb + *L0.extra_count;
+    for (int64_t j = (int64_t)blockIdx.x * BLOCK + threadIdx.x; j < r1_max; j += (int64_t)gridDim.x * BLOCK) {
+        if (j >= r_real) {
+            R1[j] = pack(j + 1 < r1_max ? (uint32_t)(j + 1) : NIL, 0);
+            continue;
+        }
+        const uint64_t w = R1[j];
+        if (lo32(w) != NIL) continue;
+        const int64_t e = splitter_node0(j, L0);
+        int64_t k = find_list(off, K, e) + 1;
+        while (k < K && off[k + 1] == off[k]) ++k;
+        uint32_t nx = NIL;
+        if (k < K) nx = (uint32_t)head_spl[k];
+        else if (r_real < r1_max) nx = (uint32_t)r_real;
+        R1[j] = pack(nx, hi32(w));
+    }
+}
+
+// Global ranks -> local ranks: subtract the elements of the later lists.
+__global__ void __launch_bounds__(BLOCK)
+    bl_fix(int32_t* __restrict__ rank, const int64_t* __restrict__ off, int64_t K, int64_t n) {
+    __shared__ int64_t s_k;
+    for (int64_t t0 = (int64_t)blockIdx.x * BL_TILE; t0 < n; t0 += (int64_t)gridDim.x * BL_TILE) {
+        if (threadIdx.x == 0) s_k = find_list(off, K, t0);
+        __syncthreads();
+        int64_t k = s_k;
+        __syncthreads();
+        for (int64_t i = t0 + threadIdx.x; i < min(t0 + BL_TILE, n); i += BLOCK) {
+            while (k + 1 < K && off[k + 1] <= i) ++k;
+            rank[i] -= (int32_t)(n - off[k + 1]);
+        }
+    }
+}
+
 // ------------------------------------------- range check of the values
 
 // Weighted ranks by the ruling set keep every partial sum in the 31-bit
@@ -1154,7 +1344,7 @@ int rs_walk_grid(Ctx* c, const Plan& p) {
     return persistent_grid(c, k, BLOCK);
 }
 
-RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid) {
+RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
     RsLayout L;
     L.size[0] = n;
     size_t off = 0;
@@ -1174,7 +1364,8 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid) {
         while (logD < 20 && (int64_t(1) << (logD + 1)) <= spacing) ++logD;
         if (lvl == MAX_LEVELS - 1)  // last allowed level must fit one block
             while (logD < 30 && ((cur + (int64_t(1) << logD) - 1) >> logD) > p.rs_small) ++logD;
-        const int64_t nb = (cur + (int64_t(1) << logD) - 1) >> logD;
+        // level 1 may hold extra splitters (the heads of batched lists ranked as one list)
+        const int64_t nb = ((cur + (int64_t(1) << logD) - 1) >> logD) + (lvl == 0 ? extra1 : 0);
         L.logD[lvl] = logD;
         ++lvl;
         L.size[lvl] = nb;
@@ -1214,12 +1405,63 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid) {
     return L;
 }
 
+// Batched lists as one list: the plan, the layout and the workspace.
+constexpr int64_t BATCH_UNION_MIN = int64_t(1) << 22;
+
+bool batch_union_applies(int64_t total, const Plan& batch_plan) {
+    return total >= BATCH_UNION_MIN && batch_plan.rs_level0 == 2;
+}
+
+struct UnionPlan {
+    Plan p;
+    RsLayout L;
+    size_t off_gsucc, off_head_spl, off_extra, off_head_dev, bytes;
+};
+
+UnionPlan union_plan(Ctx* c, int64_t total, int64_t K) {
+    UnionPlan U;
+    U.p = plan_for(KIND_LR, total);
+    U.p.rs_level0 = 2;
+    U.L = rs_layout(total, U.p, rs_walk_grid(c, U.p), K);
+    size_t off = align_up(U.L.bytes, 256);
+    U.off_gsucc = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)total, 256);
+    U.off_head_spl = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)K, 256);
+    U.off_extra = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)K, 256);
+    U.off_head_dev = off;
+    U.bytes = off + 256;
+    return U;
+}
+
+size_t lr_batched_union_ws(Ctx* c, int64_t total, int64_t K) { return union_plan(c, total, K).bytes; }
+
+lrcc_status lr_batched_union(Ctx* c, cudaStream_t s, const int32_t* succ, const int64_t* off, const int32_t* heads,
+                             int64_t K, int64_t total, int32_t* rank) {
+    const UnionPlan P = union_plan(c, total, K);
+    if (!P.L.readonly || P.L.levels == 0 || c->ws_bytes < P.bytes) return LRCC_ERR_ARG;
+    char* base = static_cast<char*>(c->ws);
+    BatchUnion U;
+    U.off = off;
+    U.heads = heads;
+    U.K = K;
+    U.gsucc = reinterpret_cast<int32_t*>(base + P.off_gsucc);
+    U.head_spl = reinterpret_cast<int32_t*>(base + P.off_head_spl);
+    U.extra_elem = reinterpret_cast<int32_t*>(base + P.off_extra);
+    U.head_dev = reinterpret_cast<int64_t*>(base + P.off_head_dev);
+    return lr_enqueue_rs(c, s, succ, total, 0, rank, P.p, P.L, nullptr, &U);
+}
+
 size_t lr_wyllie_ws(int64_t n, const Plan&) { return 2 * align_up(sizeof(uint64_t) * (size_t)n, 256); }
 
 // ------------------------------------------------------------ enqueueing
 
 lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
-                          int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val) {
+                          int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val,
+                          const BatchUnion* U) {
+    // batched lists ranked as one list need the read-only first level
+    if (U && (!L.readonly || val)) return LRCC_ERR_ARG;
     // weighted sums use the in-place first level (the read-only one counts positions)
     if (val && L.readonly) return LRCC_ERR_ARG;
     if (val) {
@@ -1255,11 +1497,23 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     }
     Level0 L0;
     L0.n = n;
-    L0.nb = L.size[1];
     L0.logD = L.logD[0];
+    L0.nb = (n + (int64_t(1) << L0.logD) - 1) >> L0.logD;   // stratified splitters (level 1 may hold more)
     L0.bh = (int64_t)head >> L0.logD;
     L0.head_off = (uint32_t)(head - (L0.bh << L0.logD));
     L0.seed = seed0;
+    if (U) {
+        const int g = stream_grid(c, (n + BL_TILE - 1) / BL_TILE * BLOCK, (const void*)bl_gsucc);
+        phase_begin(c, s);
+        bl_gsucc<<<g, BLOCK, 0, s>>>(succ, U->off, U->K, n, U->gsucc, ctl);
+        bl_heads<<<1, 1024, 0, s>>>(U->off, U->heads, U->K, n, L0.logD, L0.nb, seed0, U->head_spl, U->extra_elem,
+                                    U->head_dev, ctl);
+        phase_end(c, s, PH_BATCH_PREP);
+        succ = U->gsucc;
+        L0.head_dev = U->head_dev;
+        L0.extra = U->extra_elem;
+        L0.extra_count = &ctl->ff_extra;
+    }
     Chunks C;
     C.ids = reinterpret_cast<int32_t*>(base + L.off_ids);
     C.meta = reinterpret_cast<uint64_t*>(base + L.off_meta);
@@ -1305,6 +1559,12 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         phase_begin(c, s);
         rs_scan_counts<<<NBK, SCAN_THREADS, 0, s>>>(C.counts, L.units, C.totals);
         phase_end(c, s, PH_SCAN);
+        if (U) {
+            phase_begin(c, s);
+            bl_link<<<stream_grid(c, L.size[1], (const void*)bl_link), BLOCK, 0, s>>>(R(1), L.size[1], U->off, U->K,
+                                                                                    U->head_spl, L0, ctl);
+            phase_end(c, s, PH_BATCH_PREP);
+        }
     } else {
         walk(0, W0, n);
     }
@@ -1350,6 +1610,12 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         phase_begin(c, s);
         rs_place<<<g, BLOCK, 0, s>>>(W0, n, rank, ctl);
         phase_end(c, s, PH_EXPAND0);
+        if (U) {
+            phase_begin(c, s);
+            bl_fix<<<stream_grid(c, (n + BL_TILE - 1) / BL_TILE * BLOCK, (const void*)bl_fix), BLOCK, 0, s>>>(
+                rank, U->off, U->K, n);
+            phase_end(c, s, PH_EXPAND0);
+        }
     } else {
         const bool v = vec && aligned16(rank);
         const void* k = v ? (const void*)rs_expand0<true> : (const void*)rs_expand0<false>;

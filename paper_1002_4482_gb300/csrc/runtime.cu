@@ -504,11 +504,21 @@ lrcc_status lr_rank_batched_sized(const int32_t* succ, const int64_t* node_off, 
     lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;
     std::lock_guard<std::mutex> lk(c->mu);
-    const Plan p = plan_for(KIND_LR_BATCH, 0);
-    st = ensure_ws(c, lr_batched_ws(total_nodes, num_lists));
-    if (st != LRCC_OK) return st;
-    reset_ctl(c, c->stream);
-    st = lr_batched_run(c, succ, node_off, heads, num_lists, rank, total_nodes, p);
+    // the batched plan is looked up by the total element count: its first-level
+    // mode decides between one block per list and the lists ranked as one list
+    const Plan p = plan_for(KIND_LR_BATCH, total_nodes);
+    if (batch_union_applies(total_nodes, p)) {
+        // the lists ranked together as one list by the read-only first level
+        st = ensure_ws(c, lr_batched_union_ws(c, total_nodes, num_lists));
+        if (st != LRCC_OK) return st;
+        reset_ctl(c, c->stream);
+        st = lr_batched_union(c, c->stream, succ, node_off, heads, num_lists, total_nodes, rank);
+    } else {
+        st = ensure_ws(c, lr_batched_ws(total_nodes, num_lists));
+        if (st != LRCC_OK) return st;
+        reset_ctl(c, c->stream);
+        st = lr_batched_run(c, succ, node_off, heads, num_lists, rank, total_nodes, p);
+    }
     c->last_kind = KIND_LR_BATCH;
     return st;
 }
@@ -733,7 +743,15 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
         }
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
         case KIND_CC: return (int64_t)(p.cc_hook == 4 ? cc_sv_ws(n) : cc_ws(m));
-        case KIND_LR_BATCH: return (int64_t)lr_batched_ws(n, m);   // n = total elements, m = lists
+        case KIND_LR_BATCH: {   // n = total elements, m = lists
+            const Plan pb = plan_for(KIND_LR_BATCH, n);
+            if (!batch_union_applies(n, pb)) return (int64_t)lr_batched_ws(n, m);
+            Plan pu = plan_for(KIND_LR, n);
+            pu.rs_level0 = 2;
+            // the lists ranked as one list: the one-list layout with m extra splitters,
+            // global successors, two int32 per list (walk grid as on a GB300)
+            return (int64_t)(rs_layout(n, pu, 152 * 8, m).bytes + 4 * (size_t)n + 8 * (size_t)m + 1024);
+        }
         case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m, n);   // n = total edges, m = graphs
         default: return -1;
     }

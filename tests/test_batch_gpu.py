@@ -134,3 +134,58 @@ def test_plain_graph_entry_point_reads_total_itself():
     assert st == lrcc.OK
     lrcc.check()
     assert np.array_equal(lab.cpu().numpy(), oracle.cc_batched(src, dst, eoff, voff))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_large_batches_ranked_as_one_list(seed):
+    # at least 2^25 elements in all (where the built-in plan takes the read-only first
+    # level): the lists are linked into one list; empty lists, one-element lists,
+    # self-loop tails
+    sizes = [0, 1, 2, 5, 1000, 1 << 20, 0, 0, 3, (1 << 24) + 7, 77_777, 1] + \
+        gen.loguniform_sizes(300, 0, 16, seed).tolist() + [(1 << 24) + 1000]
+    assert sum(sizes) >= 1 << 25
+    succ, off, heads = gen.list_batch(np.asarray(sizes, np.int64), 30 + seed)
+    succ = succ.copy()
+    for k in range(0, len(sizes), 3):                   # every third list ends in a self-loop
+        b, e = off[k], off[k + 1]
+        if e > b:
+            tail = b + int(np.flatnonzero(succ[b:e] == -1)[0])
+            succ[tail] = tail - b
+    rank = lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                                torch.from_numpy(heads).to(DEV))
+    lrcc.check()
+    assert np.array_equal(rank.cpu().numpy(), oracle.lr_rank_batched(succ, off, heads))
+
+
+@pytest.mark.parametrize("case", ["cycle", "two_lists", "head_out_of_range", "succ_out_of_range"])
+def test_large_batch_invalid_instance_is_reported(case):
+    sizes = [100, 1 << 24, 50, (1 << 24) + 3]
+    succ, off, heads = gen.list_batch(np.asarray(sizes, np.int64), 40)
+    succ, heads = succ.copy(), heads.copy()
+    b, e = off[1], off[2]
+    tail = b + int(np.flatnonzero(succ[b:e] == -1)[0])
+    if case == "cycle":
+        succ[tail] = heads[1]
+    elif case == "two_lists":
+        succ[b + heads[1]] = -1
+    elif case == "head_out_of_range":
+        heads[3] = sizes[3]
+    else:
+        succ[tail] = sizes[1]
+    lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                         torch.from_numpy(heads).to(DEV))
+    assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+
+
+def test_large_batch_with_the_in_place_plan_takes_the_block_path():
+    # rs_level0 = 1 in the batched plan keeps every list on the per-block kernel
+    sizes = [1 << 24, 3, (1 << 24) + 1, 0, 999]
+    succ, off, heads = gen.list_batch(np.asarray(sizes, np.int64), 41)
+    lrcc.set_plan(lrcc.KIND_LR_BATCH, 0, 32, rs_level0=1)
+    try:
+        rank = lrcc.lr_rank_batched(torch.from_numpy(succ).to(DEV), torch.from_numpy(off).to(DEV),
+                                    torch.from_numpy(heads).to(DEV))
+        lrcc.check()
+    finally:
+        lrcc.reset_plans()
+    assert np.array_equal(rank.cpu().numpy(), oracle.lr_rank_batched(succ, off, heads))

@@ -123,8 +123,8 @@ lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t 
  * summed by pointer jumping (Sec. 3.1). When a value is negative or the values
  * total 2^31 or more, the whole forest is summed by pointer jumping instead
  * (O(n log n) work, any values). An element named by two successors, a cycle
- * or a successor out of range records LRCC_ERR_INVALID_INPUT. Workspace: about
- * 36 bytes per element (the first level is sized for every element a head).
+ * or a successor out of range records LRCC_ERR_INVALID_INPUT. Workspace: 37 to
+ * 40 bytes per element (the first level is sized for every element a head).
  */
 lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, int32_t* out, void* stream);
 
@@ -296,9 +296,9 @@ lrcc_status lrcc_release(void* stream);
 /* Bytes of device workspace (and host-call staging) currently held by the library (all streams). */
 int64_t lrcc_workspace_bytes(void);
 
-/* Device workspace a call of the given kind and size would need (batched
- * lists: n = total elements, m = lists; batched graphs: n = total edges,
- * m = graphs). */
+/* Device workspace a call of the given kind and size would need (kinds as
+ * in lrcc_stats; batched lists: n = total elements, m = lists; batched graphs:
+ * n = total edges, m = graphs; 6 = lr_scan, 7 = lr_scan_forest). */
 int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m);
 
 #ifdef __cplusplus

@@ -735,8 +735,14 @@ int64_t lrcc_workspace_bytes(void) {
 int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
     (void)m;
     if (n < 0) return -1;
-    const Plan p = plan_for(kind, n);
+    const Plan p = plan_for(kind > 5 ? KIND_LR : kind, n);
     switch (kind) {
+        case 6: {   // lr_scan: the in-place first level
+            Plan ps = p;
+            ps.rs_level0 = 1;
+            return n > ps.rs_small ? (int64_t)rs_layout(n, ps, 152 * 8).bytes : 0;
+        }
+        case 7: return (int64_t)lr_scan_forest_ws(n, p);   // lr_scan_forest
         case KIND_LR: {
             // block count of the walk as on a GB300 (152 SMs x 8 blocks) when no device is queried
             return n > p.rs_small ? (int64_t)rs_layout(n, p, 152 * 8).bytes : 0;

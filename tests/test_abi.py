@@ -132,3 +132,8 @@ def test_workspace_query(lib):
     finally:
         lrcc.set_plan(lrcc.KIND_LR, 28, 28, rs_level0=2)
     assert L.lrcc_workspace_query(lrcc.KIND_LR_WYLLIE, 1 << 20, 0) == 16 * (1 << 20)
+    # weighted ranks: the in-place first level; forests: 37 to 40 bytes per element
+    assert 8 * (1 << 24) <= L.lrcc_workspace_query(6, 1 << 24, 0) < 10 * (1 << 24)
+    assert 37 * (1 << 24) <= L.lrcc_workspace_query(7, 1 << 24, 0) < 40 * (1 << 24)
+    # batched lists of 2^26 elements in all are ranked as one list (the read-only layout)
+    assert L.lrcc_workspace_query(lrcc.KIND_LR_BATCH, 1 << 26, 4096) > 18 * (1 << 26)

@@ -670,6 +670,28 @@ def main():
                "api": "lr_rank_host + cc_label_host (host buffers; the library copies in and out)",
                "note": "pinned host buffers; consecutive steps alternate between two streams per call, so one "
                        "step's host-device copies overlap the other step's kernels"}
+        # the bound this leg meets: the box's pinned copy rates, measured on the same buffers
+        scratch = torch.empty(n_lr, dtype=torch.int32, device=dev)
+
+        def copy_gbs(dst, src):
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                for _ in range(3):
+                    dst.copy_(src, non_blocking=True)
+                c1.record(stream)
+            stream.synchronize()
+            return 3 * src.numel() * src.element_size() / (c0.elapsed_time(c1) * 1e6)
+
+        h2d_gbs = copy_gbs(scratch, succ_p)
+        d2h_gbs = copy_gbs(rank_p[0], scratch)
+        del scratch
+        bound_ms = max(e2e["h2d_bytes_per_step"] / (h2d_gbs * 1e6), e2e["d2h_bytes_per_step"] / (d2h_gbs * 1e6))
+        e2e["copy_bound"] = {"h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs, "ms_per_step": bound_ms,
+                             "frac": bound_ms / e2e_ms,
+                             "note": "pinned 1 GiB copies alone; the step cannot beat its host-to-device bytes at "
+                                     "this rate"}
         for s_ in all_streams:
             lrcc.release(s_)
         del succ_p, src_p, dst_p, rank_p, label_p

@@ -215,6 +215,16 @@ lrcc_status cc_label_batched_sized(const int32_t* src, const int32_t* dst, const
  */
 lrcc_status lrcc_last_status(void* stream);
 
+/*
+ * Check of the device-side timeout path: runs, on `stream`, the bounded wait
+ * that guards the bulk copies of lr_rank's read-only first level, on a barrier
+ * that no copy completes. After `polls` polls (1 to 2^20; others return
+ * LRCC_ERR_ARG) the wait gives up and records LRCC_ERR_TIMEOUT on the stream,
+ * as a copy that never lands would; the context stays usable. Allocates
+ * nothing beyond the stream's status word.
+ */
+lrcc_status lrcc_wait_check(int polls, void* stream);
+
 /* Statistics of the most recent call on `stream` (waits for the stream). */
 typedef struct lrcc_stats {
     int32_t kind;            /* 1 = lr_rank, 2 = lr_rank_wyllie, 3 = cc_label, 4/5 = batched,

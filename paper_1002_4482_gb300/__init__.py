@@ -32,7 +32,7 @@ KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
            "lr_rank_host", "cc_label_host", "lr_scan", "lr_scan_forest",
            "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "cc_label_batched_sized", "lrcc_last_status", "lrcc_last_stats",
-           "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans", "lrcc_release", "lrcc_workspace_bytes",
+           "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity")
 
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
         lib.cc_label_batched.argtypes = [p, p, p, p, i64, p, p]
         lib.cc_label_batched_sized.argtypes = [p, p, p, p, i64, i64, p, p]
         lib.lrcc_last_status.argtypes = [p]
+        lib.lrcc_wait_check.argtypes = [i, p]
         lib.lrcc_last_stats.argtypes = [p, ctypes.POINTER(Stats)]
         lib.lrcc_set_plan.argtypes = [i, i, i, ctypes.POINTER(Plan)]
         lib.lrcc_get_plan.argtypes = [i, i64, ctypes.POINTER(Plan)]
@@ -106,7 +107,7 @@ def load() -> ctypes.CDLL:
                   "lr_rank_batched",
                   "lr_rank_batched_sized",
                   "cc_label_batched", "cc_label_batched_sized",
-                  "lrcc_last_status", "lrcc_last_stats", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans",
+                  "lrcc_last_status", "lrcc_last_stats", "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
             getattr(lib, f).restype = i
         _lib = lib
@@ -307,6 +308,12 @@ def cc_label_batched(src: torch.Tensor, dst: torch.Tensor, edge_off: torch.Tenso
 def last_status(stream=None) -> int:
     """Waits for the stream; returns and clears its device status word."""
     return int(load().lrcc_last_status(_stream(stream)))
+
+
+def wait_check(polls: int, stream=None) -> None:
+    """Enqueues the check of the device timeout path (lrcc_wait_check): a bounded
+    wait that gives up after `polls` polls and records ERR_TIMEOUT on the stream."""
+    _call(load().lrcc_wait_check(int(polls), _stream(stream)), "lrcc_wait_check")
 
 
 def check(stream=None) -> None:

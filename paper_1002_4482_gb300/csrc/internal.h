@@ -136,6 +136,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
 size_t lr_scan_forest_ws(int64_t n, const Plan& p);
 lrcc_status lr_enqueue_scan_forest(Ctx* c, cudaStream_t s, const int32_t* succ, const int32_t* val, int64_t n,
                                    int32_t* out, const Plan& p);
+cudaError_t wait_check_enqueue(DevCtl* ctl, int polls, cudaStream_t s);
 lrcc_status lr_enqueue_wyllie(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
                               int32_t* rank, const Plan& p);
 size_t lr_wyllie_ws(int64_t n, const Plan& p);

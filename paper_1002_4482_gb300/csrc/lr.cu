@@ -575,7 +575,10 @@ constexpr int SC_U = 2;                         // chunks per thread and round
 constexpr int SC_BUF = 2;                       // rounds staged in shared memory (in flight + current)
 constexpr int SC_CHUNKS = SC_U * BLOCK;         // chunks per round
 constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
-constexpr int SC_WAIT_LIMIT = 1 << 22;          // polls of a bulk-copy barrier before giving up
+// Polls of a bulk-copy barrier before giving up. A poll that finds the phase
+// open suspends the thread for a few microseconds (about 4.3 us measured on
+// GB300), so the limit is about one second.
+constexpr int SC_WAIT_LIMIT = 1 << 18;
 struct ScatterSmem {
     int32_t ids[SC_BUF][SC_ITEMS];      // chunk ids of the round in each buffer
     uint64_t meta[SC_BUF][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
@@ -765,6 +768,28 @@ __global__ void __launch_bounds__(BLOCK, 4)
         __syncthreads();
     }
 }
+
+// Exercises the scatter's bounded wait on a barrier that no copy will ever
+// complete: one arrival announces 16 bytes of transfer and no copy is issued,
+// so the wait gives up after `polls` polls and records LRCC_ERR_TIMEOUT the
+// way the scatter does. Nothing is in flight when the block exits.
+__global__ void wait_check_kernel(DevCtl* ctl, int polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!mbar_wait_bounded(&bar, 0, polls)) record_error(ctl, LRCC_ERR_TIMEOUT, -6);
+}
+
+}  // namespace
+
+cudaError_t wait_check_enqueue(DevCtl* ctl, int polls, cudaStream_t s) {
+    wait_check_kernel<<<1, 32, 0, s>>>(ctl, polls);
+    return cudaGetLastError();
+}
+
+namespace {
 
 // rank[element] from the pairs. Blocks take slices of PLACE_SLICE pairs from
 // one counter in order, so at any moment the pairs in flight cover a few

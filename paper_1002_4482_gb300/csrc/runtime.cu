@@ -572,6 +572,15 @@ lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64
     return cc_label_batched_sized(src, dst, edge_off, vert_off, num_graphs, total, label, stream);
 }
 
+lrcc_status lrcc_wait_check(int polls, void* stream) {
+    if (polls < 1 || polls > (1 << 20)) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return cuda_status(wait_check_enqueue(c->ctl, polls, c->stream));
+}
+
 lrcc_status lrcc_last_status(void* stream) {
     Ctx* c = nullptr;
     lrcc_status st = ctx_for(stream, &c);

@@ -193,3 +193,26 @@ def test_full_size_2p28_random_and_ordered():
     rank = lrcc.lr_rank(torch.from_numpy(succ).to(DEV), head)
     lrcc.check()
     assert np.array_equal(rank.cpu().numpy(), np.arange(n - 1, -1, -1, dtype=np.int32))
+
+
+@pytest.mark.gpu
+def test_bounded_wait_records_timeout():
+    """The bounded bulk-copy wait gives up on a barrier that no copy completes, records
+    ERR_TIMEOUT on the stream and leaves the context usable (a rank call after it is exact)."""
+    assert lrcc.last_status() == lrcc.OK
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    lrcc.wait_check(1 << 10)
+    ev[1].record()
+    assert lrcc.last_status() == lrcc.ERR_TIMEOUT
+    assert lrcc.last_status() == lrcc.OK          # read and cleared
+    ev[2].record()
+    lrcc.wait_check(1 << 14)
+    ev[3].record()
+    assert lrcc.last_status() == lrcc.ERR_TIMEOUT
+    torch.cuda.synchronize()
+    print(f"bounded wait: 2^10 polls {ev[0].elapsed_time(ev[1]):.3f} ms, 2^14 polls {ev[2].elapsed_time(ev[3]):.3f} ms")
+    with pytest.raises(lrcc.LrccError):
+        lrcc.wait_check(0)
+    succ, head = gen.list_random(100_003, 5)
+    assert np.array_equal(_run("rs", succ, head), oracle.lr_rank(succ, head))

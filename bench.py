@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-families", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the list-ranking size sweep")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=400)
     ap.add_argument("--plain-launches", action="store_true",
@@ -232,41 +233,58 @@ def random_gather_peak(torch, dev, stream, log2n=28):
 
 
 def bench_lr_sweep(lrcc, torch, dev, stream, sizes=(16, 18, 20, 22, 24, 26, 28)):
-    """List-ranking throughput against list size for both first-level layouts
-    (in-place 8-byte words, read-only walk with chunked records) and both list
-    layouts (random, ordered = even splitters along the list): where the rate
-    changes as the list outgrows L2 (the paper's "inflection", Sec. 3.2)."""
+    """List-ranking throughput against list size for the three first-level layouts
+    (in-place 8-byte words, read-only walk with chunked records, split mark and
+    local-rank arrays) and both list layouts (random, ordered = even splitters along
+    the list): where the rate changes as the list outgrows L2 (the paper's
+    "inflection", Sec. 3.2). The paper's own comparison, the 48-bit split arrays
+    (16-bit marks, so fewer than 65,535 splitters) against the packed 64-bit words
+    at the same spacing, is measured on the random layout as `paper48` / `paper64`."""
     import gen
     out = []
     base = {k: lrcc.get_plan(lrcc.KIND_LR, 1 << k) for k in sizes}
+
+    def best_ms(s_d, head, r_d):
+        lrcc.lr_rank(s_d, head, out=r_d, stream=stream)
+        stream.synchronize()
+        best = float("inf")
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lrcc.lr_rank(s_d, head, out=r_d, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        lrcc.check(stream)
+        return best
+
     try:
         for lg in sizes:
             n = 1 << lg
             row = {"log2n": lg}
+            d48 = base[lg]["rs_spacing0"]
+            while (n + d48 - 1) // d48 >= 0xFFFF:
+                d48 *= 2
             for layout in ("random", "ordered"):
                 succ_h, head = gen.list_random(n, 100 + lg) if layout == "random" else gen.list_ordered(n)
                 with torch.cuda.stream(stream):
                     s_d = torch.from_numpy(succ_h).to(dev)
                     r_d = torch.empty_like(s_d)
-                for l0 in (1, 2):
-                    lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=l0)
-                    lrcc.lr_rank(s_d, head, out=r_d, stream=stream)
-                    stream.synchronize()
-                    best = float("inf")
-                    for _ in range(3):
-                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        a.record(stream)
-                        lrcc.lr_rank(s_d, head, out=r_d, stream=stream)
-                        b.record(stream)
-                        b.synchronize()
-                        best = min(best, a.elapsed_time(b))
-                    lrcc.check(stream)
-                    row[f"{layout}_{'inplace' if l0 == 1 else 'readonly'}_gnodes_per_s"] = n / best / 1e6
+                variants = [("inplace", 1, base[lg]["rs_spacing0"]), ("readonly", 2, base[lg]["rs_spacing0"]),
+                            ("split", 3, base[lg]["rs_spacing0"])]
+                if layout == "random":
+                    variants += [("paper48", 3, d48), ("paper64", 1, d48)]
+                for name, l0, d0 in variants:
+                    lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=l0, rs_spacing0=d0)
+                    row[f"{layout}_{name}_gnodes_per_s"] = n / best_ms(s_d, head, r_d) / 1e6
+                if layout == "random":
+                    row["paper48_spacing0"] = d48
                 del s_d, r_d
             out.append(row)
     finally:
         for lg in sizes:
-            lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=base[lg]["rs_level0"])
+            lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=base[lg]["rs_level0"],
+                          rs_spacing0=base[lg]["rs_spacing0"])
     return out
 
 
@@ -718,6 +736,7 @@ def main():
     families = sweep = None
     if rank == 0 and not args.no_families:
         families = bench_families(lrcc, torch, dev, stream)
+    if rank == 0 and not args.no_sweep:
         sweep = bench_lr_sweep(lrcc, torch, dev, stream, (16, 18, 20, 22, 24, 26, 28) if args.workload == "large"
                                else (12, 14, 16, 18, 20))
     if rank == 0 and not args.no_batched:

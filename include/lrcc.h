@@ -257,7 +257,11 @@ typedef struct lrcc_plan {
     int32_t rs_level0;       /* first ruling-set level: 1 = the walk rewrites 8-byte words in
                                 place; 2 = the walk only reads succ and writes what it visits
                                 as 32-byte chunks, which are turned into ranks by a scatter
-                                into id-range buckets and a placement pass */
+                                into id-range buckets and a placement pass; 3 = the walk
+                                reads succ and keeps an ownership mark (16 bits below 65,535
+                                splitters, else 32) and a local rank in two arrays (the
+                                paper's "48 bit" form, Sec. 3.2). lr_scan and lr_scan_forest
+                                always use 1 */
     uint64_t seed;           /* splitter seed (results do not depend on it) */
     int32_t cc_sample;       /* components: before the first pass over all edges, one hook pass
                                 and shortcut over the first m / cc_sample edges (a sample that

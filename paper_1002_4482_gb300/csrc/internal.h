@@ -27,7 +27,8 @@ struct Plan {
     int rs_spacing = 16;
     int rs_small = 8192;
     int rs_chains = 1;
-    int rs_level0 = 2;      // 1 = in-place walk words, 2 = read-only walk + chunked records
+    int rs_level0 = 2;      // 1 = in-place walk words, 2 = read-only walk + chunked records,
+                            // 3 = split mark / local-rank arrays
     int cc_hook = 1;
     int cc_max_rounds = 0;
     int use_graphs = 1;
@@ -47,6 +48,7 @@ struct RsLayout {
         off_S[MAX_LEVELS + 1];
     size_t off_W0 = 0;
     bool readonly = false;          // level 0 by the read-only walk (chunks, scan, scatter, place)
+    bool split = false;             // level 0 over split mark / local-rank arrays
     int64_t grid = 0, cap = 0, ovf_cap = 0;
     int segcap = 0, units = 0;
     size_t off_ids = 0, off_meta = 0, off_fill = 0, off_counts = 0, off_totals = 0,

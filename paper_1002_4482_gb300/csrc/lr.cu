@@ -16,6 +16,7 @@
 // the tail, itself included); the final rank is S - 1.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "block_wyllie.cuh"
 #include "common.cuh"
@@ -897,6 +898,162 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+// ------------------------------------------------ level 0, split arrays
+//
+// The paper's other first-level layout (Sec. 3.2, the "48 bit" version): the
+// walk reads succ itself and keeps each element's ownership mark and local
+// rank in two arrays, so a step reads succ[x] and mark[x] and writes mark[x]
+// and lrank[x] (two random reads and two random writes, where the packed
+// in-place word takes one of each). The mark is 16 bits while the level has
+// fewer than 65,535 splitters (the paper's 2 + 4 bytes per element), 32 bits
+// otherwise. A mark of all ones means "not visited"; a splitter's mark is its
+// own index and its local rank 0.
+
+template <typename MT>
+__global__ void __launch_bounds__(BLOCK)
+    rs_select0s(const int32_t* __restrict__ succ, MT* __restrict__ mark, int32_t* __restrict__ lrank,
+                int32_t* __restrict__ snext, int32_t* __restrict__ sw, Level0 L0, DevCtl* ctl) {
+    constexpr MT UNSEEN = MT(~MT(0));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; i < L0.n;
+         i += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int64_t j = splitter_index0(i, L0);
+        mark[i] = j >= 0 ? (MT)j : UNSEEN;
+        if (j >= 0) {
+            const int v = succ[i];
+            const bool tail = (v == -1) | (v == i);
+            const bool bad = !tail && (v < 0 || v >= L0.n);
+            if (bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+            snext[j] = (tail || bad) ? (int32_t)NIL : v;
+            sw[j] = 1;
+            lrank[i] = 0;
+        }
+    }
+}
+
+// Sublist walk over the split arrays; the hand-out of splitters to lanes is
+// the same as rs_walk's. Output per splitter j: R1[j] = (next splitter,
+// elements from j up to it), the packed words of level 1.
+template <typename MT, int K>
+__global__ void __launch_bounds__(BLOCK)
+    rs_walk0s(const int32_t* __restrict__ succ, MT* __restrict__ mark, int32_t* __restrict__ lrank,
+              const int32_t* __restrict__ snext, uint64_t* __restrict__ R1, int* work, Level0 L0, DevCtl* ctl) {
+    constexpr MT UNSEEN = MT(~MT(0));
+    constexpr int CHUNK = 64;
+    const int r = (int)L0.nb;
+    const int64_t n = L0.n;
+    const int lane = threadIdx.x & 31;
+    int pool = 0, pool_end = 0;
+    bool exhausted = false;
+    int j[K];
+    uint32_t cur[K], pre[K];
+    int64_t steps[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        j[q] = -1;
+        cur[q] = NIL;
+        pre[q] = 0;
+        steps[q] = 0;
+    }
+    for (;;) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            bool need = j[q] < 0;
+            unsigned m = __ballot_sync(0xffffffffu, need);
+            while (m && !exhausted) {
+                if (pool >= pool_end) {
+                    int b = 0;
+                    if (lane == 0) b = atomicAdd(work, CHUNK);
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    if (b >= r) {
+                        exhausted = true;
+                        break;
+                    }
+                    pool = b;
+                    pool_end = min(b + CHUNK, r);
+                }
+                const int avail = pool_end - pool;
+                const int rk = __popc(m & lanemask_lt());
+                if (need && rk < avail) {
+                    const int jj = pool + rk;
+                    j[q] = jj;
+                    cur[q] = (uint32_t)snext[jj];
+                    pre[q] = 1;
+                    steps[q] = 0;
+                    need = false;
+                }
+                pool += min(avail, __popc(m));
+                m = __ballot_sync(0xffffffffu, need);
+            }
+        }
+        bool act = false;
+#pragma unroll
+        for (int q = 0; q < K; ++q) act |= j[q] >= 0;
+        if (!__any_sync(0xffffffffu, act)) break;
+        MT mk[K];
+        int sx[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const bool live = j[q] >= 0 && cur[q] < (uint32_t)n;
+            mk[q] = live ? mark[cur[q]] : UNSEEN;
+            sx[q] = live ? succ[cur[q]] : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (j[q] < 0) continue;
+            if (cur[q] == NIL) {
+                R1[j[q]] = pack(NIL, pre[q]);
+                j[q] = -1;
+                continue;
+            }
+            if (cur[q] >= (uint32_t)n || ++steps[q] > n) {
+                record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)cur[q]);
+                R1[j[q]] = pack(NIL, pre[q]);
+                j[q] = -1;
+                continue;
+            }
+            if (mk[q] != UNSEEN) {
+                // a splitter ends the sublist; any other marked element was
+                // reached twice, so the input is not one list
+                if (splitter_index0(cur[q], L0) == (int64_t)mk[q]) {
+                    R1[j[q]] = pack((uint32_t)mk[q], pre[q]);
+                } else {
+                    record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)cur[q]);
+                    R1[j[q]] = pack(NIL, pre[q]);
+                }
+                j[q] = -1;
+                continue;
+            }
+            mark[cur[q]] = (MT)j[q];
+            lrank[cur[q]] = (int32_t)pre[q];
+            pre[q] += 1;
+            const int v = sx[q];
+            const bool tail = (v == -1) | ((uint32_t)v == cur[q]);
+            const bool bad = !tail && (v < 0 || v >= n);
+            if (bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)cur[q]);
+            cur[q] = (tail || bad) ? NIL : (uint32_t)v;
+        }
+    }
+}
+
+// rank = S1[mark] - lrank - 1 (RS5 over the split arrays).
+template <typename MT>
+__global__ void __launch_bounds__(BLOCK)
+    rs_expand0s(const MT* __restrict__ mark, const int32_t* __restrict__ lrank, int64_t n,
+                const int32_t* __restrict__ S1, int64_t r1, int32_t* __restrict__ rank, DevCtl* ctl) {
+    constexpr MT UNSEEN = MT(~MT(0));
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const MT m = __ldcs(mark + i);
+        if (m == UNSEEN || (int64_t)m >= r1) {
+            // never visited: not reachable from the head
+            record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+            __stcs(rank + i, -1);
+        } else {
+            __stcs(rank + i, (int32_t)((uint32_t)S1[m] - (uint32_t)__ldcs(lrank + i) - 1u));
+        }
+    }
+}
+
 // ---------------------------------------------------------------- Wyllie
 
 template <bool VEC>
@@ -1378,8 +1535,9 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
         off = align_up(off + bytes, 256);
         return o;
     };
-    // in-place walk words, or the (element, rank) pairs of the read-only walk
-    L.off_W0 = take(sizeof(uint64_t) * (size_t)n);
+    // in-place walk words, the (element, rank) pairs of the read-only walk, or
+    // the split mark and local-rank arrays (each 256-byte aligned)
+    L.off_W0 = take(sizeof(uint64_t) * (size_t)n + 256);
     int64_t cur = n;
     int lvl = 0;
     while (cur > p.rs_small && lvl < MAX_LEVELS) {
@@ -1402,6 +1560,7 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
     }
     L.levels = lvl;
     L.readonly = p.rs_level0 == 2 && lvl > 0 && walk_grid > 0;
+    L.split = p.rs_level0 == 3 && lvl > 0;
     if (L.readonly) {
         const int64_t G = walk_grid;
         L.grid = G;
@@ -1487,8 +1646,8 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
                           const BatchUnion* U) {
     // batched lists ranked as one list need the read-only first level
     if (U && (!L.readonly || val)) return LRCC_ERR_ARG;
-    // weighted sums use the in-place first level (the read-only one counts positions)
-    if (val && L.readonly) return LRCC_ERR_ARG;
+    // weighted sums use the in-place first level (the others count positions)
+    if (val && (L.readonly || L.split)) return LRCC_ERR_ARG;
     if (val) {
         phase_begin(c, s);
         rs_scan_check<<<stream_grid(c, n, (const void*)rs_scan_check), BLOCK, 0, s>>>(val, n, c->ctl);
@@ -1508,7 +1667,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     // level 0
     const bool vec = aligned16(succ) && (!val || aligned16(val));
     const int64_t groups = (n + 3) / 4;
-    if (!L.readonly) {
+    if (!L.readonly && !L.split) {
         const void* k = vec ? (const void*)rs_select0<true> : (const void*)rs_select0<false>;
         const int g = stream_grid(c, groups, k);
         phase_begin(c, s);
@@ -1538,6 +1697,23 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         L0.head_dev = U->head_dev;
         L0.extra = U->extra_elem;
         L0.extra_count = &ctl->ff_extra;
+    }
+    // split arrays: 16-bit marks while every splitter index fits below the
+    // all-ones "not visited" value
+    const bool mark16 = L.size[1] < 0xFFFF;
+    void* mark = base + L.off_W0;
+    int32_t* lrank = reinterpret_cast<int32_t*>(
+        base + L.off_W0 + align_up((mark16 ? sizeof(uint16_t) : sizeof(uint32_t)) * (size_t)n, 256));
+    if (L.split) {
+        phase_begin(c, s);
+        if (mark16) {
+            const int g = stream_grid(c, n, (const void*)rs_select0s<uint16_t>);
+            rs_select0s<uint16_t><<<g, BLOCK, 0, s>>>(succ, (uint16_t*)mark, lrank, SN(1), SW(1), L0, ctl);
+        } else {
+            const int g = stream_grid(c, n, (const void*)rs_select0s<uint32_t>);
+            rs_select0s<uint32_t><<<g, BLOCK, 0, s>>>(succ, (uint32_t*)mark, lrank, SN(1), SW(1), L0, ctl);
+        }
+        phase_end(c, s, PH_SELECT0);
     }
     Chunks C;
     C.ids = reinterpret_cast<int32_t*>(base + L.off_ids);
@@ -1590,6 +1766,24 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
                                                                                     U->head_spl, L0, ctl);
             phase_end(c, s, PH_BATCH_PREP);
         }
+    } else if (L.split) {
+        auto walk0s = [&](auto mt, auto k) {
+            using MT = decltype(mt);
+            constexpr int K = decltype(k)::value;
+            const int g = persistent_grid(c, (const void*)rs_walk0s<MT, K>, BLOCK);
+            rs_walk0s<MT, K><<<g, BLOCK, 0, s>>>(succ, (MT*)mark, lrank, SN(1), R(1), &ctl->work[0], L0, ctl);
+        };
+        phase_begin(c, s);
+        if (mark16) {
+            if (p.rs_chains >= 4) walk0s(uint16_t(), std::integral_constant<int, 4>());
+            else if (p.rs_chains == 2) walk0s(uint16_t(), std::integral_constant<int, 2>());
+            else walk0s(uint16_t(), std::integral_constant<int, 1>());
+        } else {
+            if (p.rs_chains >= 4) walk0s(uint32_t(), std::integral_constant<int, 4>());
+            else if (p.rs_chains == 2) walk0s(uint32_t(), std::integral_constant<int, 2>());
+            else walk0s(uint32_t(), std::integral_constant<int, 1>());
+        }
+        phase_end(c, s, PH_WALK0);
     } else {
         walk(0, W0, n);
     }
@@ -1641,6 +1835,16 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
                 rank, U->off, U->K, n);
             phase_end(c, s, PH_EXPAND0);
         }
+    } else if (L.split) {
+        phase_begin(c, s);
+        if (mark16) {
+            const int g = stream_grid(c, n, (const void*)rs_expand0s<uint16_t>);
+            rs_expand0s<uint16_t><<<g, BLOCK, 0, s>>>((const uint16_t*)mark, lrank, n, S(1), L.size[1], rank, ctl);
+        } else {
+            const int g = stream_grid(c, n, (const void*)rs_expand0s<uint32_t>);
+            rs_expand0s<uint32_t><<<g, BLOCK, 0, s>>>((const uint32_t*)mark, lrank, n, S(1), L.size[1], rank, ctl);
+        }
+        phase_end(c, s, PH_EXPAND0);
     } else {
         const bool v = vec && aligned16(rank);
         const void* k = v ? (const void*)rs_expand0<true> : (const void*)rs_expand0<false>;

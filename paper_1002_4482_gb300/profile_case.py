@@ -1,7 +1,7 @@
 """Run one call of the library on a seeded input, for profilers (ncu).
 
     python -m paper_1002_4482_gb300.profile_case lr 26        # lr_rank, random list of 2^26
-    python -m paper_1002_4482_gb300.profile_case lr 26 inplace    # or: readonly
+    python -m paper_1002_4482_gb300.profile_case lr 26 inplace    # or: readonly, split
     python -m paper_1002_4482_gb300.profile_case wyllie 24
     python -m paper_1002_4482_gb300.profile_case cc 22        # cc_label, R-MAT scale 22, edge factor 16
     python -m paper_1002_4482_gb300.profile_case batch 10     # 2^10 mixed instances, both batched calls
@@ -35,6 +35,8 @@ def main(argv):
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=1)
     elif variant == "readonly":
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=2)
+    elif variant == "split":
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=3)
     if what in ("lr", "wyllie"):
         succ, head, perm = gen.list_random(1 << log2, 3, with_perm=True)
         s = torch.from_numpy(succ).to(dev)

@@ -56,7 +56,7 @@ def test_selfloop_tail_convention(level0, fn):
     assert np.array_equal(_run(fn, s2, head), oracle.lr_rank(succ, head))
 
 
-@pytest.mark.parametrize("level0", [1, 2], ids=["inplace", "bucketed"])
+@pytest.mark.parametrize("level0", [1, 2, 3], ids=["inplace", "bucketed", "split"])
 def test_result_independent_of_splitters(level0):
     succ, head = gen.list_random(300_000, 4)
     expect = oracle.lr_rank(succ, head)
@@ -73,7 +73,7 @@ def test_result_independent_of_splitters(level0):
         _restore_level0()
 
 
-@pytest.fixture(params=[1, 2], ids=["inplace", "bucketed"])
+@pytest.fixture(params=[1, 2, 3], ids=["inplace", "bucketed", "split"])
 def level0(request):
     lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=request.param)
     yield request.param
@@ -140,6 +140,19 @@ def test_invalid_inputs_are_reported(level0, fn, case):
     # the stream and the library stay usable
     good, h = gen.list_random(n, 8)
     assert np.array_equal(_run(fn, good, h), oracle.lr_rank(good, h))
+
+
+def test_split_arrays_mark_width_boundary():
+    # split first level: 16-bit marks up to 65,534 splitters (indices below the
+    # all-ones "not visited" mark), 32-bit marks from 65,535 on
+    try:
+        for n in (4 * 65534, 4 * 65534 + 1, 4 * 65535, 4 * 65535 + 3, 4 * 65536 + 1):
+            lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=3, rs_spacing0=4, rs_small=1024)
+            succ, head = gen.list_random(n, 31)
+            assert np.array_equal(_run("rs", succ, head), oracle.lr_rank(succ, head)), n
+            assert lrcc.last_stats()["splitters"][0] == (n + 3) // 4
+    finally:
+        _restore_level0()
 
 
 def test_host_argument_errors():

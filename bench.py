@@ -33,6 +33,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LR Mnodes/s and CC Medges/s at 1 GB300, % of HBM roofline; batched vs per-launch"
 UNIT = "M(list nodes + graph edges)/s"
+# bytes per element that the first ruling-set level moves, by layout (plan.rs_level0)
+LR_METHOD_FIRST = {1: 40, 2: 34, 3: 38}
+LR_METHOD_NOTE = {
+    1: "select 4 B read + 8 B written, walk 8 B read + 8 B written, expand 8 B read + 4 B written",
+    2: "walk 4 B read + 5 B written, scatter 5 B read + 8 B written, placement 8 B read + 4 B written",
+    3: "select 4 B read + 4 B written, walk 8 B read + 8 B written, expand 8 B read + 4 B written",
+}
 
 # ncu DRAM bytes of one first-level walk launch (rs_walk0c) at n = 2^28, random
 # layout: dram__bytes_read.sum + dram__bytes_write.sum of a capture at n = 2^26
@@ -492,8 +499,18 @@ def main():
         lrcc.lr_rank(succ, head, out=rank_out, stream=stream)
         lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
 
-    # warm-up (also builds the graphs and the workspace)
-    for _ in range(args.warmup):
+    # warm-up (also builds the graphs and the workspace); the first call of
+    # each kind is timed on its own: it allocates the stream's workspace and
+    # captures the CUDA graphs that later calls replay
+    first_call_ms = {}
+    for kind, fn in (("lr", lambda: lrcc.lr_rank(succ, head, out=rank_out, stream=stream)),
+                     ("cc", lambda: lrcc.cc_label(src, dst, n_cc, out=label, stream=stream))):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        stream.synchronize()
+        first_call_ms[kind] = (time.perf_counter() - t0) * 1e3
+    for _ in range(args.warmup - 1):
         step()
     lrcc.check(stream)
     lr_stats = None
@@ -515,6 +532,21 @@ def main():
     clocks = clk.summary()
     ms_step = ev0.elapsed_time(ev1) / args.steps
     lrcc.check(stream)
+
+    # the same steps timed one by one (20 runs, as the paper averages 20):
+    # median and minimum
+    per_step = []
+    for _ in range(20):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        per_step.append(a.elapsed_time(b))
+    lrcc.check(stream)
+    per_step.sort()
+    step_stats = {"runs": len(per_step), "median_ms": (per_step[9] + per_step[10]) / 2, "min_ms": per_step[0],
+                  "max_ms": per_step[-1]}
 
     # second timed pass of K steps with the library's phase timing on: CUDA
     # events on the launching stream around every kernel (plain launches),
@@ -551,6 +583,9 @@ def main():
     hbm, peak_kind = peaks()
     roofline = None
     level0 = lrcc.get_plan(lrcc.KIND_LR, n_lr)["rs_level0"]
+    # bytes the method moves: per element of each ruling-set level, per edge read by a hook pass
+    lr_method = LR_METHOD_FIRST[level0] * n_lr + 44 * sum(lr_stats["splitters"])
+    cc_method = 16 * cc_stats["edges_read"] + 8 * n_cc * cc_stats["rounds"] + 4 * n_cc
     if "rs_walk0" in phases:
         wt, wl = phases["rs_walk0"]
         per_launch_ms = wt / wl
@@ -760,12 +795,23 @@ def main():
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generators in gen/)",
                 "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_lr + launches_cc,
                 "roofline": roofline, "cpu_baseline": cpu,
+                "step_ms": step_stats, "first_call_ms": first_call_ms,
                 "lr": {"ms": lr_ms, "mnodes_per_s": n_lr / lr_ms / 1e3 if lr_ms else None,
                        "problem_bytes_frac": 8 * n_lr / (lr_ms / 1e3) / 1e9 / hbm if lr_ms else None,
+                       "method_bytes_per_node": lr_method / n_lr,
+                       "method_bytes_frac": lr_method / (lr_ms / 1e3) / 1e9 / hbm if lr_ms else None,
+                       "method_bytes_note": "first level: " + LR_METHOD_NOTE[level0] + "; each deeper level: "
+                                            "8 B read + 8 B written by the select and the walk, 8 B read + "
+                                            "4 B written by the expand, per element of the level",
                        "levels": lr_stats["levels"], "splitters": lr_stats["splitters"]},
                 "cc": {"ms": cc_ms, "medges_per_s": m_cc / cc_ms / 1e3 if cc_ms else None,
                        "problem_bytes_frac": (8 * m_cc + 4 * n_cc) / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
-                       "rounds": cc_stats["rounds"]},
+                       "rounds": cc_stats["rounds"], "edges_read": cc_stats["edges_read"],
+                       "method_bytes": cc_method,
+                       "method_bytes_frac": cc_method / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
+                       "method_bytes_note": "16 B per edge read by a hook pass (8 B of edge, two 4-byte parent "
+                                            "gathers), 8 B per vertex and shortcut pass, 4 B per vertex of init; "
+                                            "R = rounds"},
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
                 "batched": batched, "serving": serving, "cc_families": families, "lr_sweep": sweep,
                 **extra}

@@ -235,6 +235,8 @@ typedef struct lrcc_stats {
     int32_t jump_rounds;     /* lr_rank_wyllie: pointer-jumping rounds */
     int64_t overflow_chunks; /* lr_rank, read-only first level: 8-element chunks that did not fit
                                 their walk block's region and went to the shared overflow pool */
+    int64_t edges_read;      /* cc_label (hook rules 1-3): edges read by all hook passes, the
+                                sample pass and the compacted active edges included */
 } lrcc_stats;
 lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out);
 

@@ -46,7 +46,8 @@ class LrccError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("splitters", ctypes.c_int64 * 8), ("rounds", ctypes.c_int32),
-                ("jump_rounds", ctypes.c_int32), ("overflow_chunks", ctypes.c_int64)]
+                ("jump_rounds", ctypes.c_int32), ("overflow_chunks", ctypes.c_int64),
+                ("edges_read", ctypes.c_int64)]
 
 
 class Plan(ctypes.Structure):
@@ -327,7 +328,8 @@ def last_stats(stream=None) -> dict:
     s = Stats()
     _call(load().lrcc_last_stats(_stream(stream), ctypes.byref(s)), "lrcc_last_stats")
     return {"kind": s.kind, "levels": s.levels, "splitters": list(s.splitters)[: s.levels],
-            "rounds": s.rounds, "jump_rounds": s.jump_rounds, "overflow_chunks": s.overflow_chunks}
+            "rounds": s.rounds, "jump_rounds": s.jump_rounds, "overflow_chunks": s.overflow_chunks,
+            "edges_read": s.edges_read}
 
 
 def set_plan(kind: int, log2_lo: int = 0, log2_hi: int = 32, **fields) -> None:

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(BLOCK, 6)
     int2* out = act.cap > 0 ? act.buf[out_sel - 1] : nullptr;
     const int lane = threadIdx.x & 31;
     const int64_t ngroups = (me + 3) >> 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->edges_read, (unsigned long long)me);
     bool changed = false;
     // each warp stages its active edges in shared memory and appends them in
     // batches (one counter atomic per batch, coalesced writes), so that a pass

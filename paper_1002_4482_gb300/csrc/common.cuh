@@ -33,6 +33,7 @@ struct DevCtl {
     int ff_extra;        // forest ranks: list heads that became extra first-level splitters
     int pad[1];
     unsigned long long scan_total;   // weighted ranks: sum of the values
+    unsigned long long edges_read;   // component loop: edges read by all hook passes
 };
 
 __device__ __forceinline__ void record_error(DevCtl* c, int code, int where = -1) {

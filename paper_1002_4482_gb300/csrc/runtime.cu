@@ -609,6 +609,7 @@ lrcc_status lrcc_last_stats(void* stream, lrcc_stats* out) {
     out->rounds = h.rounds;
     out->jump_rounds = h.jump_rounds;
     out->overflow_chunks = h.ovf_next;
+    out->edges_read = (int64_t)h.edges_read;
     return LRCC_OK;
 }
 

@@ -153,6 +153,22 @@ def test_sample_pass_keeps_labels(hook, sample):
         lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=base)
 
 
+def test_stats_count_edges_read():
+    # no sample pass: the first pass reads every edge, each later pass at most all of them;
+    # with the sample pass of m/16 edges, that prefix is read once more
+    src, dst = gen.er(1 << 16, 1 << 20, 45)
+    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 16)["cc_sample"]
+    try:
+        for sample, extra in ((1, 0), (16, (1 << 20) // 16)):
+            lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=sample, cc_hook=1)
+            assert np.array_equal(_run(src, dst, 1 << 16), oracle.cc_uf(src, dst, 1 << 16))
+            st = lrcc.last_stats()
+            assert (1 << 20) + extra <= st["edges_read"] <= st["rounds"] * (1 << 20) + extra, (sample, st)
+    finally:
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=base)
+        lrcc.reset_plans()
+
+
 @pytest.mark.parametrize("family", ["lists", "trees-2", "trees-5", "trees-20", "density-0.001", "density-0.01"])
 def test_paper_graph_families(hook, family):
     # the families of the paper's component experiments (Sec. 4): collections of

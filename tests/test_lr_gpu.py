@@ -196,11 +196,21 @@ def test_full_size_2p28_random_and_ordered():
     n = 1 << 28
     succ, head, perm = workloads.lr_random(28, with_perm=True)
     t = torch.from_numpy(succ).to(DEV)
+    expect = np.arange(n - 1, -1, -1, dtype=np.int32)
     rank = lrcc.lr_rank(t, head)
     lrcc.check()
     r = rank.cpu().numpy()
-    assert np.array_equal(r[perm], np.arange(n - 1, -1, -1, dtype=np.int32))
+    assert np.array_equal(r[perm], expect)
     pins.lr_sample(succ, head, r, 1 << 22, 0)
+    # the other first-level layouts at the same size: in-place words, split arrays
+    try:
+        for level0 in (1, 3):
+            lrcc.set_plan(lrcc.KIND_LR, 28, 28, rs_level0=level0)
+            rank = lrcc.lr_rank(t, head, out=rank)
+            lrcc.check()
+            assert np.array_equal(rank.cpu().numpy()[perm], expect), level0
+    finally:
+        _restore_level0()
     del t, rank
     succ, head = workloads.lr_ordered(28)
     rank = lrcc.lr_rank(torch.from_numpy(succ).to(DEV), head)

@@ -489,28 +489,18 @@ def main():
         return
 
     import torch
-    import torch.distributed as dist
 
     import paper_1002_4482_gb300 as lrcc
+    from paper_1002_4482_gb300 import ranks
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = ranks.env()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    ranks.init("nccl", dev)
+    barrier = ranks.barrier
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks.max_over_ranks(x, dev)
 
     if args.plain_launches:
         for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC):
@@ -848,8 +838,7 @@ def main():
                 "batched": batched, "serving": serving, "cc_families": families, "lr_sweep": sweep,
                 **extra}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.shutdown()
 
 
 if __name__ == "__main__":

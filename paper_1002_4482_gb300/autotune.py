@@ -51,7 +51,9 @@ def _timeit(fn, stream, reps=3):
 
 
 def _lr_candidates(log2n, quick):
-    level0 = (1, 2) if log2n >= 22 else (1,)
+    # first-level layouts: in-place words, read-only walk (from 2^22), and in the
+    # full search the split mark / rank arrays as well
+    level0 = ((1, 2) if log2n >= 22 else (1,)) + (() if quick else (3,))
     sp0 = (8, 32) if quick else (8, 16, 32, 64)
     sp = (8,) if quick else (8, 16, 32)
     small = (16384,) if quick else (4096, 8192, 16384)

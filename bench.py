@@ -92,16 +92,18 @@ def workload(name):
     return succ, head, src, dst, n_cc, cfg
 
 
-def cpu_sample(name):
-    """Bounded sample of the workload for the oracle (about 10 s of CPU work)."""
+def cpu_sample(name, log2s=26):
+    """Bounded sample of the workload for the oracle: a 2^log2s-element list and
+    the first 2^log2s edges of the graph, the workload's 1:1 mix of list
+    elements and edges (2^26: about 12 s of one Arm core)."""
     from gen import workloads
     import gen
     if name == "large":
-        succ, head = gen.list_random(1 << 25, 3)
+        succ, head = gen.list_random(1 << log2s, 3)
         src, dst, n_cc = workloads.cc_rmat(24, 16)
-        src, dst = src[: 1 << 24].copy(), dst[: 1 << 24].copy()
-        desc = ("oracle walk of a 2^25-element random-layout list + union-find over the first 2^24 edges "
-                "of the R-MAT scale-24 edge list (2^24 vertices)")
+        src, dst = src[: 1 << log2s].copy(), dst[: 1 << log2s].copy()
+        desc = (f"oracle walk of a 2^{log2s}-element random-layout list + union-find over the first "
+                f"2^{log2s} edges of the R-MAT scale-24 edge list (2^24 vertices)")
     else:
         succ, head = workloads.lr_random(20)
         src, dst, n_cc = workloads.cc_er(20, 22)
@@ -195,7 +197,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sample = cpu_sample(args.workload)
+    # one step is a bounded sample, halved for every doubling of the run's
+    # steps beyond 13, so that the whole run stays within a few minutes
+    log2s = 26 - max(0, math.ceil(math.log2(max(1, args.steps + args.warmup) / 13)))
+    sample = cpu_sample(args.workload, max(22, log2s))
     units = len(sample[0]) + len(sample[2])
     for _ in range(args.warmup):
         time_oracle(sample)

@@ -1167,9 +1167,10 @@ __global__ void __launch_bounds__(BLOCK)
 // that is another element); after the walk, the splitter that ends list k is
 // linked to the head splitter of the next non-empty list, and the unused extra
 // slots become a tail of empty splitters. Ranks along that one list are the
-// local ranks plus the number of elements of the later lists, which a last
-// pass subtracts. A walk never steps onto a head (nothing names it), so the
-// walk recognises splitters by their hash as for one list.
+// local ranks plus the number of elements of the later lists, which are taken
+// off the first-level splitters' suffix sums before the scatter. A walk never
+// steps onto a head (nothing names it), so the walk recognises splitters by
+// their hash as for one list.
 
 // The list that holds element i (for empty lists, the last list starting at i).
 __device__ __forceinline__ int64_t find_list(const int64_t* __restrict__ off, int64_t K, int64_t i) {
@@ -1184,24 +1185,37 @@ __device__ __forceinline__ int64_t find_list(const int64_t* __restrict__ off, in
 
 constexpr int BL_TILE = BLOCK * 16;
 
-// Global successors; one binary search per tile of elements.
+// Global successors; one binary search per tile of elements. Each thread
+// loads its 16 elements of the tile first, so that 16 streaming reads are in
+// flight, then converts them.
 __global__ void __launch_bounds__(BLOCK)
     bl_gsucc(const int32_t* __restrict__ succ, const int64_t* __restrict__ off, int64_t K, int64_t n,
              int32_t* __restrict__ gsucc, DevCtl* ctl) {
+    constexpr int PER = BL_TILE / BLOCK;
     __shared__ int64_t s_k;
+    const uint64_t pol = policy_evict_first();
     for (int64_t t0 = (int64_t)blockIdx.x * BL_TILE; t0 < n; t0 += (int64_t)gridDim.x * BL_TILE) {
         if (threadIdx.x == 0) s_k = find_list(off, K, t0);
         __syncthreads();
         int64_t k = s_k;
         __syncthreads();
-        for (int64_t i = t0 + threadIdx.x; i < min(t0 + BL_TILE, n); i += BLOCK) {
+        const int64_t tend = min(t0 + BL_TILE, n);
+        int32_t sx[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int64_t i = t0 + threadIdx.x + (int64_t)q * BLOCK;
+            sx[q] = i < tend ? ld_stream(succ + i, pol) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int64_t i = t0 + threadIdx.x + (int64_t)q * BLOCK;
+            if (i >= tend) break;
             while (k + 1 < K && off[k + 1] <= i) ++k;
             const int64_t base = off[k], len = off[k + 1] - base;
-            const int32_t sx = succ[i];
             int32_t g = -1;
-            if (sx != -1 && sx != i - base) {
-                if (sx < 0 || sx >= len) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
-                else g = (int32_t)(base + sx);
+            if (sx[q] != -1 && sx[q] != i - base) {
+                if (sx[q] < 0 || sx[q] >= len) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
+                else g = (int32_t)(base + sx[q]);
             }
             gsucc[i] = g;
         }
@@ -1319,19 +1333,22 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
-// Global ranks -> local ranks: subtract the elements of the later lists.
+// Global ranks -> local ranks: every element of list k is ahead of the
+// n - off[k + 1] elements of the later lists, which its local rank does not
+// count. A sublist never leaves its list (each list ends in a tail), so the
+// correction is taken once per first-level splitter, from its suffix sum,
+// before the scatter turns suffix sums into ranks.
 __global__ void __launch_bounds__(BLOCK)
-    bl_fix(int32_t* __restrict__ rank, const int64_t* __restrict__ off, int64_t K, int64_t n) {
-    __shared__ int64_t s_k;
-    for (int64_t t0 = (int64_t)blockIdx.x * BL_TILE; t0 < n; t0 += (int64_t)gridDim.x * BL_TILE) {
-        if (threadIdx.x == 0) s_k = find_list(off, K, t0);
-        __syncthreads();
-        int64_t k = s_k;
-        __syncthreads();
-        for (int64_t i = t0 + threadIdx.x; i < min(t0 + BL_TILE, n); i += BLOCK) {
-            while (k + 1 < K && off[k + 1] <= i) ++k;
-            rank[i] -= (int32_t)(n - off[k + 1]);
-        }
+    bl_adjust(int32_t* __restrict__ S1, const int64_t* __restrict__ off, int64_t K, int64_t n, Level0 L0) {
+    const int64_t gh = *L0.head_dev;
+    L0.bh = gh >> L0.logD;
+    L0.head_off = (uint32_t)(gh - (L0.bh << L0.logD));
+    const int64_t r_real = L0.nb + *L0.extra_count;   // the empty tail splitters own nothing
+    for (int64_t j = (int64_t)blockIdx.x * BLOCK + threadIdx.x; j < r_real; j += (int64_t)gridDim.x * BLOCK) {
+        const int64_t e = splitter_node0(j, L0);
+        if (e < 0 || e >= n) continue;
+        const int64_t k = find_list(off, K, e);
+        S1[j] = (int32_t)((uint32_t)S1[j] - (uint32_t)(n - off[k + 1]));
     }
 }
 
@@ -1819,6 +1836,11 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         rs_expand<<<g, BLOCK, 0, s>>>(R(l), (int)L.size[l], S(l + 1), (int)L.size[l + 1], S(l), ctl);
         phase_end(c, s, PH_EXPAND);
     }
+    if (U) {
+        phase_begin(c, s);
+        bl_adjust<<<stream_grid(c, L.size[1], (const void*)bl_adjust), BLOCK, 0, s>>>(S(1), U->off, U->K, n, L0);
+        phase_end(c, s, PH_BATCH_PREP);
+    }
     if (L.readonly) {
         phase_begin(c, s);
         cudaFuncSetAttribute((const void*)rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM);
@@ -1829,12 +1851,6 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         phase_begin(c, s);
         rs_place<<<g, BLOCK, 0, s>>>(W0, n, rank, ctl);
         phase_end(c, s, PH_EXPAND0);
-        if (U) {
-            phase_begin(c, s);
-            bl_fix<<<stream_grid(c, (n + BL_TILE - 1) / BL_TILE * BLOCK, (const void*)bl_fix), BLOCK, 0, s>>>(
-                rank, U->off, U->K, n);
-            phase_end(c, s, PH_EXPAND0);
-        }
     } else if (L.split) {
         phase_begin(c, s);
         if (mark16) {

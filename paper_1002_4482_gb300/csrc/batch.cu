@@ -406,18 +406,62 @@ __device__ __forceinline__ int seg_find(const int64_t* pre, int nl, int64_t x) {
 
 constexpr int SEG_RUN = 8;   // consecutive vertices or edges per thread
 
+// Vertex passes over the large instances take tiles of SEG_TILE union
+// positions x (one binary search per tile); thread t handles x = t0 + t +
+// q * SEG_BLOCK, so consecutive threads touch consecutive vertices.
+constexpr int SEG_PER = 16;
+constexpr int64_t SEG_TILE = (int64_t)SEG_BLOCK * SEG_PER;
+
 // label[g] = g for every vertex g of a large instance (g = voff[k] + local).
 __global__ void __launch_bounds__(SEG_BLOCK) seg_init(LargeSet L, const int64_t* __restrict__ voff, int32_t* label) {
+    __shared__ int s_i;
     const int nl = *L.nlarge;
     const int64_t V = L.lvp[nl];
-    for (int64_t x0 = ((int64_t)blockIdx.x * SEG_BLOCK + threadIdx.x) * SEG_RUN; x0 < V;
-         x0 += (int64_t)gridDim.x * SEG_BLOCK * SEG_RUN) {
-        int i = seg_find(L.lvp, nl, x0);
-        for (int64_t x = x0; x < min(x0 + SEG_RUN, V); ++x) {
+    for (int64_t t0 = (int64_t)blockIdx.x * SEG_TILE; t0 < V; t0 += (int64_t)gridDim.x * SEG_TILE) {
+        if (threadIdx.x == 0) s_i = seg_find(L.lvp, nl, t0);
+        __syncthreads();
+        int i = s_i;
+        __syncthreads();
+        const int64_t tend = min(t0 + SEG_TILE, V);
+#pragma unroll
+        for (int q = 0; q < SEG_PER; ++q) {
+            const int64_t x = t0 + threadIdx.x + (int64_t)q * SEG_BLOCK;
+            if (x >= tend) break;
             while (x >= L.lvp[i + 1]) ++i;
             const int64_t g = voff[L.ids[i]] + (x - L.lvp[i]);
             label[g] = (int32_t)g;
         }
+    }
+}
+
+// Global labels -> local labels (label[g] - voff[k]); the tile's labels are
+// loaded first, so that SEG_PER reads are in flight.
+__global__ void __launch_bounds__(SEG_BLOCK) seg_finalize(LargeSet L, const int64_t* __restrict__ voff, int32_t* label) {
+    __shared__ int s_i;
+    const int nl = *L.nlarge;
+    const int64_t V = L.lvp[nl];
+    for (int64_t t0 = (int64_t)blockIdx.x * SEG_TILE; t0 < V; t0 += (int64_t)gridDim.x * SEG_TILE) {
+        if (threadIdx.x == 0) s_i = seg_find(L.lvp, nl, t0);
+        __syncthreads();
+        int i = s_i;
+        __syncthreads();
+        const int64_t tend = min(t0 + SEG_TILE, V);
+        int64_t g[SEG_PER], base[SEG_PER];
+        int32_t v[SEG_PER];
+#pragma unroll
+        for (int q = 0; q < SEG_PER; ++q) {
+            const int64_t x = t0 + threadIdx.x + (int64_t)q * SEG_BLOCK;
+            g[q] = -1;
+            if (x >= tend) continue;
+            while (x >= L.lvp[i + 1]) ++i;
+            base[q] = voff[L.ids[i]];
+            g[q] = base[q] + (x - L.lvp[i]);
+        }
+#pragma unroll
+        for (int q = 0; q < SEG_PER; ++q) v[q] = g[q] >= 0 ? label[g[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < SEG_PER; ++q)
+            if (g[q] >= 0) label[g[q]] = (int32_t)(v[q] - base[q]);
     }
 }
 
@@ -588,18 +632,17 @@ __global__ void seg_control_host(DevCtl* ctl, int cap, bool compacting) {
 }
 
 // Pointer jumping to stars over the large instances' vertices (skipped after
-// the pass that joined nothing); with finalize, global labels become local.
-template <bool FINALIZE>
+// the pass that joined nothing). Blocks take slices in order, so the chases in
+// flight stay within a few graphs whose parent entries L2 holds.
 __global__ void __launch_bounds__(SEG_BLOCK)
     seg_shortcut(LargeSet L, const int64_t* __restrict__ voff, int32_t* label, DevCtl* ctl) {
     __shared__ int s_slice;
-    if (!FINALIZE && ctl->cc_stop) return;
+    if (ctl->cc_stop) return;
     const uint64_t keep = policy_evict_last();
     const int nl = *L.nlarge;
     const int64_t V = L.lvp[nl];
-    int* counter = FINALIZE ? &ctl->seg_next : &ctl->seg_next_v;
     for (;;) {
-        if (threadIdx.x == 0) s_slice = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) s_slice = atomicAdd(&ctl->seg_next_v, 1);
         __syncthreads();
         const int64_t start = (int64_t)s_slice * SEG_SLICE;
         __syncthreads();
@@ -608,16 +651,11 @@ __global__ void __launch_bounds__(SEG_BLOCK)
         int i = start + threadIdx.x < end ? seg_find(L.lvp, nl, start + threadIdx.x) : 0;
         for (int64_t x = start + threadIdx.x; x < end; x += SEG_BLOCK) {
             while (x >= L.lvp[i + 1]) ++i;
-            const int64_t base = voff[L.ids[i]];
-            const int64_t g = base + (x - L.lvp[i]);
-            if (FINALIZE) {
-                label[g] = (int32_t)(label[g] - base);
-            } else {
-                const int p = label[g];
-                if (p != g) {
-                    const int r = find_root(label, p, keep);
-                    if (r != p) label[g] = r;
-                }
+            const int64_t g = voff[L.ids[i]] + (x - L.lvp[i]);
+            const int p = label[g];
+            if (p != g) {
+                const int r = find_root(label, p, keep);
+                if (r != p) label[g] = r;
             }
         }
     }
@@ -694,7 +732,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
 
     // the union of the large graphs: init, device-side loop, finalize
     const int gs = persistent_grid(c, (const void*)seg_hook, SEG_BLOCK);
-    const int gv = persistent_grid(c, (const void*)seg_shortcut<false>, SEG_BLOCK);
+    const int gv = persistent_grid(c, (const void*)seg_shortcut, SEG_BLOCK);
     const int cap = 64 + 4 * 31;
     phase_begin(c, s);
     seg_init<<<gv, SEG_BLOCK, 0, s>>>(L, voff, label);
@@ -706,7 +744,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
         for (int r = 0; r <= cap; ++r) {
             seg_hook<<<gs, SEG_BLOCK, 0, s>>>(L, src, dst, eoff, voff, label, act, p.cc_hook, c->ctl);
             seg_control_host<<<1, 1, 0, s>>>(c->ctl, cap, act.cap > 0);
-            seg_shortcut<false><<<gv, SEG_BLOCK, 0, s>>>(L, voff, label, c->ctl);
+            seg_shortcut<<<gv, SEG_BLOCK, 0, s>>>(L, voff, label, c->ctl);
             cudaMemcpyAsync(host_flag, &c->ctl->pad[0], sizeof(int), cudaMemcpyDeviceToHost, s);
             if (cudaStreamSynchronize(s) != cudaSuccess) {
                 st = LRCC_ERR_CUDA;
@@ -747,7 +785,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
             } else {
                 seg_hook<<<gs, SEG_BLOCK, 0, c->capture>>>(L, src, dst, eoff, voff, label, act, p.cc_hook, c->ctl);
                 seg_control<<<1, 1, 0, c->capture>>>(c->ctl, h, cap, act.cap > 0);
-                seg_shortcut<false><<<gv, SEG_BLOCK, 0, c->capture>>>(L, voff, label, c->ctl);
+                seg_shortcut<<<gv, SEG_BLOCK, 0, c->capture>>>(L, voff, label, c->ctl);
                 cudaGraph_t captured = nullptr;
                 if (cudaStreamEndCapture(c->capture, &captured) != cudaSuccess) st = LRCC_ERR_CUDA;
             }
@@ -770,7 +808,7 @@ lrcc_status cc_batched_run(Ctx* c, const int32_t* src, const int32_t* dst, const
     e->last_use = ++c->tick;
     if (cudaGraphLaunch(e->exec, s) != cudaSuccess) return LRCC_ERR_CUDA;
     }
-    seg_shortcut<true><<<gv, SEG_BLOCK, 0, s>>>(L, voff, label, c->ctl);
+    seg_finalize<<<gv, SEG_BLOCK, 0, s>>>(L, voff, label);
     phase_end(c, s, PH_CC_LOOP);
 
     // every other graph: one block each, largest first

@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(SEG_BLOCK)
     seg_hook(LargeSet L, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
              const int64_t* __restrict__ eoff, const int64_t* __restrict__ voff, int32_t* label, SegActive act,
              int mode, DevCtl* ctl) {
-    __shared__ int s_slice;
+    __shared__ int s_slice, s_i;
     const bool relink = mode == 2 || (mode == 3 && ctl->rounds > 0);
     const uint64_t keep = policy_evict_last();
     const uint64_t stream_pol = policy_evict_first();
@@ -515,14 +515,17 @@ __global__ void __launch_bounds__(SEG_BLOCK)
         staged = 0;
     };
     for (;;) {
-        if (threadIdx.x == 0) s_slice = atomicAdd(&ctl->seg_next, 1);
+        if (threadIdx.x == 0) {
+            s_slice = atomicAdd(&ctl->seg_next, 1);
+            const int64_t st = (int64_t)s_slice * SEG_SLICE;
+            s_i = sel == 0 && st < E ? seg_find(L.lep, nl, st) : 0;
+        }
         __syncthreads();
         const int64_t start = (int64_t)s_slice * SEG_SLICE;
+        int i = s_i;   // the slice's first graph; each thread advances from it
         __syncthreads();
         if (start >= E) break;
         const int64_t end = min(start + SEG_SLICE, E);
-        int i = 0;
-        if (sel == 0 && start + threadIdx.x < end) i = seg_find(L.lep, nl, start + threadIdx.x);
         for (int64_t c0 = start; c0 < end; c0 += (int64_t)SEG_BLOCK * SEG_RUN) {
             int32_t u[SEG_RUN], v[SEG_RUN];
 #pragma unroll
@@ -636,19 +639,23 @@ __global__ void seg_control_host(DevCtl* ctl, int cap, bool compacting) {
 // flight stay within a few graphs whose parent entries L2 holds.
 __global__ void __launch_bounds__(SEG_BLOCK)
     seg_shortcut(LargeSet L, const int64_t* __restrict__ voff, int32_t* label, DevCtl* ctl) {
-    __shared__ int s_slice;
+    __shared__ int s_slice, s_i;
     if (ctl->cc_stop) return;
     const uint64_t keep = policy_evict_last();
     const int nl = *L.nlarge;
     const int64_t V = L.lvp[nl];
     for (;;) {
-        if (threadIdx.x == 0) s_slice = atomicAdd(&ctl->seg_next_v, 1);
+        if (threadIdx.x == 0) {
+            s_slice = atomicAdd(&ctl->seg_next_v, 1);
+            const int64_t st = (int64_t)s_slice * SEG_SLICE;
+            s_i = st < V ? seg_find(L.lvp, nl, st) : 0;
+        }
         __syncthreads();
         const int64_t start = (int64_t)s_slice * SEG_SLICE;
+        int i = s_i;
         __syncthreads();
         if (start >= V) break;
         const int64_t end = min(start + SEG_SLICE, V);
-        int i = start + threadIdx.x < end ? seg_find(L.lvp, nl, start + threadIdx.x) : 0;
         for (int64_t x = start + threadIdx.x; x < end; x += SEG_BLOCK) {
             while (x >= L.lvp[i + 1]) ++i;
             const int64_t g = voff[L.ids[i]] + (x - L.lvp[i]);

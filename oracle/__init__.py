@@ -2,8 +2,8 @@
 
 Plain sequential C (``oracle.c``, compiled with gcc on first use) that computes
 the definitions of list ranking (Sec. 3) and connected components (Sec. 4).
-Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may use it; the library never does, and it shares no code with
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg and the
+reference arm of ``bench.py`` may use it; the library never does, and it shares no code with
 the CUDA path.
 """
 from __future__ import annotations

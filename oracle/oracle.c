@@ -2,7 +2,8 @@
  * CPU oracle for list ranking and connected components.
  *
  * TEST INFRASTRUCTURE ONLY. Nothing in the library calls this code: only the
- * tests, the smoke check and the CPU-baseline leg of the benchmark load it.
+ * tests, the smoke check and the benchmark's CPU-baseline leg and reference
+ * arm load it.
  * It shares no code, header, table or helper with the CUDA path.
  *
  * Both problems have exact, unique answers, so the oracle computes the plain

@@ -53,7 +53,7 @@ def _load():
             lib.gen_rmat.argtypes = [ctypes.c_int, i64, dbl, dbl, dbl, u64, p, p]
             lib.gen_rmat.restype = ctypes.c_int
             lib.gen_loguniform_sizes.argtypes = [i64, dbl, dbl, u64, p]
-            lib.gen_list_batch.argtypes = [i64, p, u64, p, p, p]
+            lib.gen_list_batch.argtypes = [i64, p, u64, p, p, p, p]
             lib.gen_list_batch.restype = ctypes.c_int
             lib.gen_er_batch.argtypes = [i64, p, i64, i64, u64, p, p, p, p]
             lib.gen_jobs.argtypes = [i64, dbl, dbl, dbl, dbl, u64, p, p, p]
@@ -149,17 +149,20 @@ def loguniform_sizes(count: int, lo: float, hi: float, seed: int) -> np.ndarray:
     return s
 
 
-def list_batch(sizes: np.ndarray, seed: int):
-    """Concatenated random lists: returns (succ, node_off, heads), local ids."""
+def list_batch(sizes: np.ndarray, seed: int, with_perm: bool = False):
+    """Concatenated random lists: returns (succ, node_off, heads), local ids,
+    plus, with ``with_perm``, the concatenated per-list permutations (list k
+    visits perm[node_off[k]], perm[node_off[k] + 1], ... in local ids)."""
     lib = _load()
     sizes = np.ascontiguousarray(sizes, np.int64)
     count = len(sizes)
     off = np.empty(count + 1, np.int64)
     succ = np.empty(int(sizes.sum()), np.int32)
     heads = np.empty(count, np.int32)
-    if lib.gen_list_batch(count, _ptr(sizes), seed, _ptr(off), _ptr(succ), _ptr(heads)):
+    perm = np.empty(len(succ), np.int32) if with_perm else None
+    if lib.gen_list_batch(count, _ptr(sizes), seed, _ptr(off), _ptr(succ), _ptr(heads), _ptr(perm)):
         raise MemoryError("gen_list_batch failed")
-    return succ, off, heads
+    return (succ, off, heads, perm) if with_perm else (succ, off, heads)
 
 
 def er_batch(vsizes: np.ndarray, deg_num: int, deg_den: int, seed: int):

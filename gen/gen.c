@@ -169,15 +169,18 @@ void gen_loguniform_sizes(int64_t count, double lo, double hi, uint64_t seed, in
  * A batch of independent random lists, concatenated. List k owns nodes
  * [off[k], off[k+1]) of succ; succ values and heads are LOCAL ids (0-based
  * within the list). off must hold count+1 entries and is filled from sizes.
+ * perm (may be NULL) receives each list's permutation at the list's own
+ * offset, in local ids: list k visits perm[off[k]], perm[off[k] + 1], ...
  */
 int gen_list_batch(int64_t count, const int64_t* sizes, uint64_t seed,
-                   int64_t* off, int32_t* succ, int32_t* heads) {
+                   int64_t* off, int32_t* succ, int32_t* heads, int32_t* perm) {
     off[0] = 0;
     for (int64_t k = 0; k < count; ++k) off[k + 1] = off[k] + sizes[k];
     int rc = 0;
     #pragma omp parallel for schedule(dynamic, 4) reduction(|:rc)
     for (int64_t k = 0; k < count; ++k)
-        rc |= gen_list_random(sizes[k], derive(seed, 1000 + (uint64_t)k), succ + off[k], heads + k, NULL);
+        rc |= gen_list_random(sizes[k], derive(seed, 1000 + (uint64_t)k), succ + off[k], heads + k,
+                              perm ? perm + off[k] : NULL);
     return rc;
 }
 

@@ -48,10 +48,11 @@ def batch_sizes(count: int, lo: float = 8.0, hi: float = 20.0, seed: int = 5) ->
     return loguniform_sizes(count, lo, hi, seed)
 
 
-def batch(count: int = 4096, lo: float = 8.0, hi: float = 20.0, seed: int = 5):
-    """Half lists (even instance index), half graphs with m = 2n (odd index)."""
+def batch(count: int = 4096, lo: float = 8.0, hi: float = 20.0, seed: int = 5, with_perm: bool = False):
+    """Half lists (even instance index), half graphs with m = 2n (odd index).
+    With ``with_perm`` the list part also carries each list's permutation."""
     sizes = batch_sizes(count, lo, hi, seed)
-    lists = list_batch(sizes[0::2], seed * 7919 + 1)
+    lists = list_batch(sizes[0::2], seed * 7919 + 1, with_perm)
     graphs = er_batch(sizes[1::2], 2, 1, seed * 7919 + 2)
     return lists, graphs
 

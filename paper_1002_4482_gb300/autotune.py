@@ -3,8 +3,16 @@
 For each size class it times candidate plans on seeded synthetic inputs of
 that size and installs the fastest one with ``set_plan`` for the size range
 the class stands for. Every candidate's output is checked before its time
-counts (list ranks against the generator's closed form, component labels by
-the min-id invariants), so a wrong plan can never win.
+counts, so a wrong plan can never win:
+
+  lists       ranks against the generator's closed form: the generator returns
+              the permutation it laid each list out by, and the element at
+              position k of a list of n elements has rank n - 1 - k;
+  graphs      labels equal, element by element, to those of the reference plan
+              (hook rule 1, no sample pass, plain launches: the simplest form of
+              the method, the one the parity tests pin), computed once per input
+              on the GPU before any candidate runs. Min-id labels are unique, so
+              a candidate that merges or splits a component differs there.
 
 Knobs searched:
   lists       first-level mode (in-place words / read-only walk), spacing at the
@@ -102,6 +110,20 @@ def tune_lists(classes=(16, 20, 24, 28), quick=False, device=0, log=print):
     return results
 
 
+# Plan the tuner takes the expected component labels from.
+REFERENCE_CC = {"cc_hook": 1, "cc_sample": 1, "use_graphs": 2}
+
+
+def _reference_labels(kind, log2_lo, log2_hi, run):
+    """Labels of `run()` under the reference plan, with the plan table restored after."""
+    saved = get_plan(kind, 1 << log2_lo)
+    set_plan(kind, log2_lo, log2_hi, **REFERENCE_CC)
+    try:
+        return run().clone()
+    finally:
+        set_plan(kind, log2_lo, log2_hi, **{k: saved[k] for k in ("cc_hook", "cc_sample", "use_graphs")})
+
+
 def tune_graphs(classes=(16, 20, 24), device=0, log=print):
     import gen
     from gen import workloads
@@ -117,18 +139,25 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print):
             for s_, d_, n_ in ((src1, dst1, n1), (src2, dst2, 1 << c)):
                 cases.append((torch.from_numpy(s_).to(dev), torch.from_numpy(d_).to(dev), n_,
                               torch.empty(n_, dtype=torch.int32, device=dev), s_, d_))
+        expect = []
+        for sd, dd, n_, lab, _, _ in cases:
+            def run(sd=sd, dd=dd, n_=n_, lab=lab):
+                cc_label(sd, dd, n_, out=lab, stream=stream)
+                stream.synchronize()
+                check(stream)
+                return lab
+            expect.append(_reference_labels(KIND_CC, c, c, run))
         best = None
         for hook, samp in itertools.product((1, 2, 3), (-1, 1, 4, 8)):
-            set_plan(KIND_CC, c, c, cc_hook=hook, cc_sample=samp)
+            set_plan(KIND_CC, c, c, cc_hook=hook, cc_sample=samp, use_graphs=1)
             ms = 0.0
-            for sd, dd, n_, lab, s_np, d_np in cases:
+            for (sd, dd, n_, lab, _, _), want in zip(cases, expect):
                 ms += _timeit(lambda: cc_label(sd, dd, n_, out=lab, stream=stream), stream)
                 with torch.cuda.stream(stream):
-                    ok = bool(torch.equal(lab[sd.long()], lab[dd.long()])) and \
-                        bool((lab <= torch.arange(n_, device=dev, dtype=torch.int32)).all()) and \
-                        bool(torch.equal(lab[lab.long()], lab))
+                    ok = bool(torch.equal(lab, want))
                 if not ok:
-                    raise AssertionError(f"hook rule {hook}, sample {samp} broke the label invariants at 2^{c}")
+                    raise AssertionError(f"hook rule {hook}, sample {samp} gave labels unlike the reference "
+                                         f"plan's at 2^{c}")
             if best is None or ms < best[0]:
                 best = (ms, {"cc_hook": hook, "cc_sample": samp})
         set_plan(KIND_CC, lo, hi, **best[1])
@@ -137,19 +166,36 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print):
     return results
 
 
+def _batch_expected_ranks(off: np.ndarray, perm: np.ndarray) -> np.ndarray:
+    """Closed form of batched random lists: the element at position j of list k
+    (local id perm[off[k] + j]) has rank size_k - 1 - j."""
+    total = int(off[-1])
+    sizes = np.diff(off)
+    start = np.repeat(off[:-1], sizes)
+    end = np.repeat(off[1:], sizes)
+    want = np.empty(total, np.int32)
+    want[start + perm] = (end - 1 - np.arange(total, dtype=np.int64)).astype(np.int32)
+    return want
+
+
 def tune_batched(log2_count=10, device=0, log=print):
-    import oracle
     from gen import workloads
     dev = torch.device("cuda", device)
     stream = torch.cuda.Stream(dev)
-    (succ, off, heads), (src, dst, eoff, voff) = workloads.batch(1 << log2_count)
+    (succ, off, heads, perm), (src, dst, eoff, voff) = workloads.batch(1 << log2_count, with_perm=True)
     with torch.cuda.stream(stream):
         S, O, H = (torch.from_numpy(x).to(dev) for x in (succ, off, heads))
         SR, DS, EO, VO = (torch.from_numpy(x).to(dev) for x in (src, dst, eoff, voff))
         rank = torch.empty_like(S)
         lab = torch.empty(int(voff[-1]), dtype=torch.int32, device=dev)
-    want_r = oracle.lr_rank_batched(succ, off, heads)
-    want_l = oracle.cc_batched(src, dst, eoff, voff)
+    want_r = _batch_expected_ranks(off, perm)
+
+    def run_graphs():
+        cc_label_batched(SR, DS, EO, VO, n_total=int(voff[-1]), out=lab, stream=stream)
+        stream.synchronize()
+        check(stream)
+        return lab
+    want_l = _reference_labels(KIND_CC_BATCH, 0, 32, run_graphs).cpu().numpy()
     res = {}
     best = None
     for d in (4, 16, 64):

@@ -6,9 +6,12 @@ above its successor.
 
 Connected components (Sec. 4) with min-id labels: both endpoints of an edge
 share a label, every label is at most its vertex id, labels are fixed points
-(label[label[v]] = label[v]), and every component is connected, which is
+(label[label[v]] = label[v]), and no two components share a label, which is
 checked by counting: the number of distinct labels equals n minus the number
-of successful unions of a spanning forest.
+of successful unions of a spanning forest of the edges. The first three
+properties say that every component lies inside one label class and that the
+label is the class's smallest member; the count then says that no class holds
+two components.
 """
 from __future__ import annotations
 
@@ -30,6 +33,42 @@ def lr_invariants(succ: np.ndarray, head: int, rank: np.ndarray) -> None:
     assert rank[head] == n - 1, "head rank is not n-1"
 
 
+def spanning_forest_unions(src: np.ndarray, dst: np.ndarray, n: int) -> int:
+    """Number of edges a spanning forest of the graph keeps (n minus the
+    number of components).
+
+    Built by rounds over a forest of parent pointers that always point to a
+    smaller id: find every vertex's root (pointer jumping), drop the edges
+    whose ends share a root, and give every root that is the larger end of a
+    remaining edge the smallest root it meets as its parent. Each root that
+    receives a parent joins two different trees, so counting them counts the
+    successful unions; each round hooks at least one root, so the rounds end."""
+    parent = np.arange(n, dtype=np.int64)
+    u = np.asarray(src, np.int64)
+    w = np.asarray(dst, np.int64)
+    keep = u != w
+    u, w = u[keep], w[keep]
+    unions = 0
+    while len(u):
+        while True:
+            gp = parent[parent]
+            if np.array_equal(gp, parent):
+                break
+            parent = gp
+        ru, rw = parent[u], parent[w]
+        diff = ru != rw
+        u, w, ru, rw = u[diff], w[diff], ru[diff], rw[diff]
+        if len(u) == 0:
+            break
+        hi, lo = np.maximum(ru, rw), np.minimum(ru, rw)
+        best = np.full(n, n, dtype=np.int64)
+        np.minimum.at(best, hi, lo)
+        hooked = np.flatnonzero(best < n)
+        parent[hooked] = best[hooked]
+        unions += len(hooked)
+    return unions
+
+
 def cc_invariants(src: np.ndarray, dst: np.ndarray, n: int, label: np.ndarray) -> None:
     assert label.shape == (n,)
     if n == 0:
@@ -38,6 +77,8 @@ def cc_invariants(src: np.ndarray, dst: np.ndarray, n: int, label: np.ndarray) -
     assert (label >= 0).all() and (label <= v).all(), "label outside [0, v]"
     assert np.array_equal(label[label], label), "labels are not fixed points"
     assert np.array_equal(label[src], label[dst]), "an edge joins two labels"
+    classes = len(np.unique(label))
+    assert classes == n - spanning_forest_unions(src, dst, n), "a label class holds more than one component"
 
 
 def lr_sample(succ: np.ndarray, head: int, rank: np.ndarray, samples: int, seed: int) -> None:

@@ -57,6 +57,17 @@ def test_batch_generators():
     assert sizes.min() >= 256 and sizes.max() < (1 << 20)
     succ, off, heads = gen.list_batch(np.array([3, 1, 5]), 1)
     assert off.tolist() == [0, 3, 4, 9]
+    # the permutations returned beside the lists are the order each list is visited in
+    s2, o2, h2, perm = gen.list_batch(np.array([3, 1, 5]), 1, with_perm=True)
+    assert np.array_equal(s2, succ) and np.array_equal(h2, heads)
+    for k in range(3):
+        p = perm[off[k]:off[k + 1]]
+        assert sorted(p.tolist()) == list(range(off[k + 1] - off[k])) and p[0] == heads[k]
+        walk, cur = [], heads[k]
+        while cur != -1:
+            walk.append(cur)
+            cur = succ[off[k] + cur]
+        assert walk == p.tolist()
     src, dst, eoff, voff = gen.er_batch(np.array([10, 4]), 2, 1, 1)
     assert eoff.tolist() == [0, 20, 28] and voff.tolist() == [0, 10, 14]
     assert src[:20].max() < 10 and src[20:].max() < 4
@@ -104,3 +115,13 @@ def test_density_vertices():
     assert gen.density_vertices(8_000_000, 0.001) == 126492
     n = gen.density_vertices(10_000, 0.01)
     assert abs(10_000 / (n * (n - 1) / 2) - 0.01) < 2e-4
+
+
+def test_batched_closed_form_matches_oracle():
+    # the autotuner checks batched ranks by the generator's closed form; pin
+    # that form against the oracle's walk of every list
+    import oracle
+    from paper_1002_4482_gb300.autotune import _batch_expected_ranks
+    sizes = gen.loguniform_sizes(40, 0, 9, 11)
+    succ, off, heads, perm = gen.list_batch(sizes, 12, with_perm=True)
+    assert np.array_equal(_batch_expected_ranks(off, perm), oracle.lr_rank_batched(succ, off, heads))

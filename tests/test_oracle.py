@@ -330,6 +330,23 @@ def test_cc_er_isolated_fraction():
     assert singletons.sum() >= isolated
 
 
+def test_spanning_forest_count_matches_scipy():
+    # the component count behind cc_invariants, against scipy on graphs with
+    # many components, long paths, stars and self-loops
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    cases = [gen.er(3000, 1200, 1), gen.er(500, 5000, 2)]
+    s, d, n = gen.list_graph(7, 300, 3)
+    cases.append((s, d))
+    star = np.arange(1, 400, dtype=np.int32)
+    cases.append((star, np.zeros_like(star)))
+    cases.append((np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    for (s, d), nv in zip(cases, (3000, 500, n, 400, 9)):
+        g = coo_matrix((np.ones(len(s)), (s, d)), shape=(nv, nv))
+        k = connected_components(g, directed=False)[0]
+        assert pins.spanning_forest_unions(s, d, nv) == nv - k
+
+
 def test_cc_edge_cases():
     e = np.empty(0, np.int32)
     assert np.array_equal(oracle.cc_uf(e, e, 5), np.arange(5))
@@ -350,7 +367,12 @@ def test_cc_pins_reject_mutants():
     members = np.flatnonzero(good == big)
     split = good.copy()
     split[members[1:][::2]] = members[1]          # a component broken in two
-    mutants = [np.maximum(good, v), v.copy(), split]
+    zeros = np.zeros(2000, good.dtype)            # every vertex in one class
+    roots = np.unique(good)
+    a, b = roots[0], roots[1]
+    merged = good.copy()
+    merged[good == b] = a                         # two components under one label
+    mutants = [np.maximum(good, v), v.copy(), split, zeros, merged]
     for bad in mutants:
         with pytest.raises(AssertionError):
             pins.cc_invariants(src, dst, 2000, bad)

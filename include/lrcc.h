@@ -43,7 +43,7 @@ typedef enum lrcc_status {
 } lrcc_status;
 
 /* Human-readable name of a status code. Never NULL. */
-const char* lrcc_status_str(int status);
+const char* lrcc_status_str(lrcc_status status);
 
 /* ABI version of this header (major * 100 + minor). */
 int lrcc_version(void);
@@ -305,6 +305,37 @@ lrcc_status lrcc_phase_times(void* stream, double* ms_total, int64_t* launches);
  */
 lrcc_status lrcc_set_l2_fetch_granularity(int bytes);
 int lrcc_get_l2_fetch_granularity(void);
+
+/*
+ * Contexts: an explicit handle on the library's workspaces of one device, for
+ * callers that account for device memory themselves (a serving loop with a
+ * memory budget). The compute calls above keep taking only a stream; the
+ * state a call uses is the workspace of (current device, stream). A context
+ * adopts the workspaces of the streams it reserves for, so that their bytes
+ * can be counted and freed together.
+ *
+ * lrcc_ctx_create     a context for `device` (0 .. device count - 1); nothing is
+ *                     allocated until a reservation. LRCC_ERR_ARG for a bad device.
+ * lrcc_ctx_reserve    allocates the workspace of (ctx's device, stream) now, at
+ *                     least `bytes` large (lrcc_workspace_query gives the bytes a
+ *                     call needs), so that later calls on that stream of up to
+ *                     that size allocate nothing; it waits for the stream when an
+ *                     existing workspace has to grow. LRCC_ERR_NOMEM when the
+ *                     allocation fails (the stream keeps no workspace then).
+ * lrcc_ctx_bytes      device bytes held by the workspaces the context adopted
+ *                     (kernel workspace, host-call staging and the status word of
+ *                     each stream, including growth by later calls); -1 for NULL.
+ * lrcc_ctx_last_status  lrcc_last_status for `stream` on the context's device.
+ * lrcc_ctx_destroy    waits for each adopted stream and frees its workspace and
+ *                     cached graphs, then the handle. NULL is ignored.
+ * The device is made current only for the duration of each call.
+ */
+typedef struct lrcc_ctx lrcc_ctx;
+lrcc_status lrcc_ctx_create(lrcc_ctx** ctx, int device);
+lrcc_status lrcc_ctx_reserve(lrcc_ctx* ctx, void* stream, int64_t bytes);
+int64_t lrcc_ctx_bytes(lrcc_ctx* ctx);
+lrcc_status lrcc_ctx_last_status(lrcc_ctx* ctx, void* stream);
+void lrcc_ctx_destroy(lrcc_ctx* ctx);
 
 /* Frees the workspace and cached graphs of `stream` (waits for it first). */
 lrcc_status lrcc_release(void* stream);

@@ -34,7 +34,8 @@ SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_r
            "lr_rank_batched", "lr_rank_batched_sized", "cc_label_batched", "cc_label_batched_sized", "lrcc_last_status", "lrcc_last_stats",
            "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
-           "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity")
+           "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity",
+           "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_bytes", "lrcc_ctx_last_status", "lrcc_ctx_destroy")
 
 
 class LrccError(RuntimeError):
@@ -103,13 +104,21 @@ def load() -> ctypes.CDLL:
         lib.lrcc_phase_times.argtypes = [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.lrcc_set_l2_fetch_granularity.argtypes = [i]
         lib.lrcc_get_l2_fetch_granularity.restype = i
+        lib.lrcc_ctx_create.argtypes = [ctypes.POINTER(p), i]
+        lib.lrcc_ctx_reserve.argtypes = [p, p, i64]
+        lib.lrcc_ctx_bytes.argtypes = [p]
+        lib.lrcc_ctx_bytes.restype = i64
+        lib.lrcc_ctx_last_status.argtypes = [p, p]
+        lib.lrcc_ctx_destroy.argtypes = [p]
+        lib.lrcc_ctx_destroy.restype = None
         for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_host", "cc_label_host",
                   "lr_scan", "lr_scan_forest",
                   "lr_rank_batched",
                   "lr_rank_batched_sized",
                   "cc_label_batched", "cc_label_batched_sized",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans",
-                  "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity"):
+                  "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity",
+                  "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_last_status"):
             getattr(lib, f).restype = i
         _lib = lib
         return lib
@@ -382,3 +391,35 @@ def set_l2_fetch_granularity(nbytes: int) -> None:
 
 def get_l2_fetch_granularity() -> int:
     return int(load().lrcc_get_l2_fetch_granularity())
+
+
+class Context:
+    """Handle on the library's workspaces of one device (lrcc_ctx_*): reserve a
+    stream's workspace ahead of the calls, count the bytes held, free them
+    together. The compute calls keep taking a stream."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _call(load().lrcc_ctx_create(ctypes.byref(h), int(device)), "lrcc_ctx_create")
+        self._h = h
+        self.device = int(device)
+
+    def reserve(self, stream, nbytes: int) -> None:
+        _call(load().lrcc_ctx_reserve(self._h, _stream(stream), int(nbytes)), "lrcc_ctx_reserve")
+
+    def bytes(self) -> int:
+        return int(load().lrcc_ctx_bytes(self._h))
+
+    def last_status(self, stream=None) -> int:
+        return int(load().lrcc_ctx_last_status(self._h, _stream(stream)))
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            load().lrcc_ctx_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -72,6 +72,9 @@ struct BatchUnion {
     int64_t* head_dev = nullptr;
 };
 int rs_walk_grid(Ctx* c, const Plan& p);
+// The same grid for the current device without a workspace (152 x 8 when no
+// device can be queried).
+int rs_walk_grid_current(const Plan& p);
 
 // Phase ids for timing mode (names in runtime.cu).
 enum Phase {
@@ -121,6 +124,12 @@ void phase_end(Ctx* c, cudaStream_t s, int phase);
 
 // Returns the workspace of `stream` on the current device, creating it.
 lrcc_status ctx_for(void* stream, Ctx** out);
+// The same for an explicit device (which the caller has made current).
+lrcc_status ctx_for_device(int dev, void* stream, Ctx** out);
+// Frees the workspace of (dev, stream) after waiting for the stream (dev current).
+void release_device_stream(int dev, void* stream);
+// Device bytes held by one workspace: kernel workspace, host-call staging, control block.
+int64_t ctx_bytes(const Ctx* c);
 lrcc_status ensure_ws(Ctx* c, size_t bytes);
 lrcc_status cuda_status(cudaError_t e);
 

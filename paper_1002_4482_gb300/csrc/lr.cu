@@ -1543,6 +1543,20 @@ int rs_walk_grid(Ctx* c, const Plan& p) {
     return persistent_grid(c, k, BLOCK);
 }
 
+int rs_walk_grid_current(const Plan& p) {
+    int dev = 0, sms = 0, per_sm = 0;
+    const void* k = p.rs_chains >= 4 ? (const void*)rs_walk0c<4>
+                  : p.rs_chains == 2 ? (const void*)rs_walk0c<2> : (const void*)rs_walk0c<1>;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, 0) != cudaSuccess || per_sm < 1 ||
+        sms < 1) {
+        cudaGetLastError();
+        return 152 * 8;
+    }
+    return per_sm * sms;
+}
+
 RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
     RsLayout L;
     L.size[0] = n;

@@ -7,6 +7,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <new>
 #include <utility>
 
 #include "common.cuh"
@@ -183,6 +184,10 @@ int persistent_grid(Ctx* c, const void* kernel, int block, size_t smem) {
 lrcc_status ctx_for(void* stream, Ctx** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LRCC_ERR_CUDA;
+    return ctx_for_device(dev, stream, out);
+}
+
+lrcc_status ctx_for_device(int dev, void* stream, Ctx** out) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(g_mu);
     auto key = std::make_pair(dev, s);
@@ -312,7 +317,7 @@ using namespace lrcc;
 
 extern "C" {
 
-const char* lrcc_status_str(int status) {
+const char* lrcc_status_str(lrcc_status status) {
     switch (status) {
         case LRCC_OK: return "ok";
         case LRCC_ERR_ARG: return "bad argument";
@@ -714,11 +719,22 @@ lrcc_status lrcc_phase_times(void* stream, double* ms_total, int64_t* launches) 
 lrcc_status lrcc_release(void* stream) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LRCC_ERR_CUDA;
+    release_device_stream(dev, stream);
+    return LRCC_OK;
+}
+
+}  // extern "C"
+
+namespace lrcc {
+
+// Frees the workspace of (device, stream), if any, after waiting for the
+// stream. The caller has that device current.
+void release_device_stream(int dev, void* stream) {
     Ctx* c = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_ctx.find(std::make_pair(dev, static_cast<cudaStream_t>(stream)));
-        if (it == g_ctx.end()) return LRCC_OK;
+        if (it == g_ctx.end()) return;
         c = it->second;
         g_ctx.erase(it);
     }
@@ -732,13 +748,103 @@ lrcc_status lrcc_release(void* stream) {
     cudaFree(c->ctl);
     cudaStreamDestroy(c->capture);
     delete c;
+}
+
+int64_t ctx_bytes(const Ctx* c) { return (int64_t)(c->ws_bytes + c->io_bytes) + (int64_t)sizeof(DevCtl); }
+
+}  // namespace lrcc
+
+// A context: the streams of one device whose workspaces were reserved through
+// it (the workspaces themselves stay in the per-(device, stream) table).
+struct lrcc_ctx {
+    int device = 0;
+    std::mutex mu;
+    std::vector<cudaStream_t> streams;
+};
+
+namespace {
+// Makes `dev` current for the guard's lifetime and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
+extern "C" {
+
+lrcc_status lrcc_ctx_create(lrcc_ctx** ctx, int device) {
+    if (!ctx) return LRCC_ERR_ARG;
+    *ctx = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return LRCC_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return LRCC_ERR_ARG;
+    lrcc_ctx* c = new (std::nothrow) lrcc_ctx();
+    if (!c) return LRCC_ERR_NOMEM;
+    c->device = device;
+    *ctx = c;
     return LRCC_OK;
+}
+
+void lrcc_ctx_destroy(lrcc_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (g.ok)
+            for (cudaStream_t s : ctx->streams) release_device_stream(ctx->device, s);
+    }
+    delete ctx;
+}
+
+lrcc_status lrcc_ctx_reserve(lrcc_ctx* ctx, void* stream, int64_t bytes) {
+    if (!ctx || bytes < 0) return LRCC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return LRCC_ERR_CUDA;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for_device(ctx->device, stream, &c);
+    if (st != LRCC_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        st = ensure_ws(c, (size_t)bytes);
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (std::find(ctx->streams.begin(), ctx->streams.end(), s) == ctx->streams.end()) ctx->streams.push_back(s);
+    return st;
+}
+
+int64_t lrcc_ctx_bytes(lrcc_ctx* ctx) {
+    if (!ctx) return -1;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::lock_guard<std::mutex> lk2(g_mu);
+    int64_t t = 0;
+    for (cudaStream_t s : ctx->streams) {
+        auto it = g_ctx.find(std::make_pair(ctx->device, s));
+        if (it != g_ctx.end()) t += ctx_bytes(it->second);
+    }
+    return t;
+}
+
+lrcc_status lrcc_ctx_last_status(lrcc_ctx* ctx, void* stream) {
+    if (!ctx) return LRCC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return LRCC_ERR_CUDA;
+    return lrcc_last_status(stream);
 }
 
 int64_t lrcc_workspace_bytes(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     int64_t t = 0;
-    for (auto& kv : g_ctx) t += (int64_t)(kv.second->ws_bytes + kv.second->io_bytes) + (int64_t)sizeof(DevCtl);
+    for (auto& kv : g_ctx) t += ctx_bytes(kv.second);
     return t;
 }
 
@@ -750,12 +856,12 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
         case 6: {   // lr_scan: the in-place first level
             Plan ps = p;
             ps.rs_level0 = 1;
-            return n > ps.rs_small ? (int64_t)rs_layout(n, ps, 152 * 8).bytes : 0;
+            return n > ps.rs_small ? (int64_t)rs_layout(n, ps, rs_walk_grid_current(ps)).bytes : 0;
         }
         case 7: return (int64_t)lr_scan_forest_ws(n, p);   // lr_scan_forest
         case KIND_LR: {
-            // block count of the walk as on a GB300 (152 SMs x 8 blocks) when no device is queried
-            return n > p.rs_small ? (int64_t)rs_layout(n, p, 152 * 8).bytes : 0;
+            // the walk's block count on the current device (as on a GB300 when none can be queried)
+            return n > p.rs_small ? (int64_t)rs_layout(n, p, rs_walk_grid_current(p)).bytes : 0;
         }
         case KIND_LR_WYLLIE: return n > p.rs_small ? (int64_t)lr_wyllie_ws(n, p) : 0;
         case KIND_CC: return (int64_t)(p.cc_hook == 4 ? cc_sv_ws(n) : cc_ws(m));
@@ -765,8 +871,8 @@ int64_t lrcc_workspace_query(int kind, int64_t n, int64_t m) {
             Plan pu = plan_for(KIND_LR, n);
             pu.rs_level0 = 2;
             // the lists ranked as one list: the one-list layout with m extra splitters,
-            // global successors, two int32 per list (walk grid as on a GB300)
-            return (int64_t)(rs_layout(n, pu, 152 * 8, m).bytes + 4 * (size_t)n + 8 * (size_t)m + 1024);
+            // global successors, two int32 per list
+            return (int64_t)(rs_layout(n, pu, rs_walk_grid_current(pu), m).bytes + 4 * (size_t)n + 8 * (size_t)m + 1024);
         }
         case KIND_CC_BATCH: return (int64_t)cc_batched_ws(m, n);   // n = total edges, m = graphs
         default: return -1;

@@ -4,10 +4,14 @@ Jobs are submitted from any thread and return a :class:`concurrent.futures.Futur
 that resolves to the result as a host ``numpy.int32`` array (ranks, or min-id
 component labels). A scheduler thread runs the loop:
 
-* admission  a job is admitted once its device bytes (inputs, output and its
-             share of the kernel workspace) fit in the free part of the memory
-             budget; admitted jobs keep their arrays resident on the device
-             until they complete;
+* admission  a launch unit is admitted once its jobs' device bytes (inputs and
+             outputs) plus the growth of its stream's kernel workspace fit in
+             the free part of the memory budget. The workspace a unit needs
+             comes from the library (``workspace_query``); each stream's
+             workspace is reserved through a library context before the unit
+             is launched, and the bytes the context holds (``Context.bytes``)
+             count against the budget. Admitted jobs keep their arrays resident
+             on the device until they complete;
 * batching   whenever a stream of the pool is idle, the jobs waiting at that
              moment form the next launch unit: up to ``max_batch`` small jobs of
              one kind (at most ``small_cutoff`` elements) are concatenated and
@@ -34,7 +38,8 @@ import time
 import numpy as np
 import torch
 
-from . import cc_label, cc_label_batched, check, lr_rank, lr_rank_batched
+from . import (KIND_CC, KIND_CC_BATCH, KIND_LR, KIND_LR_BATCH, Context, cc_label, cc_label_batched, check,
+               lr_rank, lr_rank_batched, workspace_query)
 
 LIST, GRAPH = 0, 1
 
@@ -59,10 +64,8 @@ class Job:
         return 4 * (self.n if self.kind == LIST else 2 * self.m)
 
     def device_bytes(self) -> int:
-        # inputs + output + workspace (the read-only ruling set needs up to
-        # ~22 bytes per element; batched and graph jobs far less)
-        work = 22 * self.n if self.kind == LIST else 0
-        return self.in_bytes() + 4 * self.n + work
+        # resident arrays: inputs + output (kernel workspace is the stream's, counted apart)
+        return self.in_bytes() + 4 * self.n
 
 
 @dataclasses.dataclass
@@ -98,6 +101,11 @@ class Server:
         self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self.out_host = [torch.empty(out_cap, dtype=torch.int32).pin_memory() for _ in range(streams)]
         self.busy = [False] * streams
+        self.ctx = Context(self.device.index if self.device.index is not None else 0)
+        for st in self.streams:                    # the context adopts every stream's workspace
+            self.ctx.reserve(st, 0)
+        self.ws_bytes = self.ctx.bytes()           # bytes the library context holds (all streams)
+        self.ws_cap = [0] * streams                # kernel workspace bytes each stream holds
         self.pending: collections.deque[Job] = collections.deque()
         self.inflight: list[_Unit] = []
         self.used = 0
@@ -144,6 +152,7 @@ class Server:
             self.stop_flag = True
             self.wake.notify()
         self.thread.join()
+        self.ctx.close()
 
     def stats(self) -> dict:
         with self.lock:
@@ -155,20 +164,35 @@ class Server:
         elems = sum(j.n + j.m for j in jobs)
         return {"jobs": len(jobs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "jobs_per_s": len(jobs) / span, "melems_per_s": elems / span / 1e6,
-                "errors": self.errors}
+                "errors": self.errors, "workspace_bytes": self.ws_bytes}
 
     # ---------------------------------------------------------- internals
-    def _take_unit(self):
-        """Pick the next launch unit from the waiting jobs (lock held)."""
+    def _unit_ws(self, jobs: list) -> int:
+        """Kernel workspace the library needs for this launch unit."""
+        if len(jobs) == 1 and jobs[0].n > self.small_cutoff:
+            j = jobs[0]
+            return workspace_query(KIND_LR, j.n) if j.kind == LIST else workspace_query(KIND_CC, j.n, j.m)
+        if jobs[0].kind == LIST:
+            return workspace_query(KIND_LR_BATCH, sum(j.n for j in jobs), len(jobs))
+        return workspace_query(KIND_CC_BATCH, sum(j.m for j in jobs), len(jobs))
+
+    def _ws_growth(self, slot: int, need: int) -> int:
+        # a workspace grows to at least 1.25x its size (the library's growth rule)
+        old = self.ws_cap[slot]
+        return 0 if need <= old else max(need, old + old // 4) - old
+
+    def _take_unit(self, slot: int):
+        """Pick the next launch unit for `slot` from the waiting jobs (lock held)."""
         if not self.pending:
             return None
         first = self.pending[0]
-        free = self.mem_budget - self.used
+        free = self.mem_budget - self.used - self.ws_bytes
         if first.n > self.small_cutoff:
-            if first.device_bytes() > free:
+            need = self._unit_ws([first])
+            if first.device_bytes() + self._ws_growth(slot, need) > free:
                 return None
             self.pending.popleft()
-            return [first]
+            return [first], need
         # a batch of small jobs of the first job's kind, in arrival order
         unit, bytes_, elems = [], 0, 0
         rest = collections.deque()
@@ -183,14 +207,28 @@ class Server:
             unit.append(j)
             bytes_ += j.device_bytes()
             elems += j.n
+        # leave jobs out (newest first) until the workspace growth fits as well
+        need = self._unit_ws(unit) if unit else 0
+        while unit and bytes_ + self._ws_growth(slot, need) > free:
+            j = unit.pop()
+            bytes_ -= j.device_bytes()
+            rest.appendleft(j)
+            need = self._unit_ws(unit) if unit else 0
         rest.extend(self.pending)
         self.pending = rest
-        return unit or None
+        return (unit, need) if unit else None
 
-    def _launch(self, jobs: list, slot: int) -> _Unit:
+    def _launch(self, jobs: list, slot: int, need: int) -> _Unit:
         stream = self.streams[slot]
         dev = self.device
         keep = []
+        if need > self.ws_cap[slot]:
+            # grow the stream's workspace through the context (the stream is idle)
+            self.ctx.reserve(stream, need)
+            held = self.ctx.bytes()
+            with self.lock:
+                self.ws_cap[slot] += held - self.ws_bytes
+                self.ws_bytes = held
         with torch.cuda.stream(stream):
             if len(jobs) == 1 and jobs[0].n > self.small_cutoff:
                 j = jobs[0]
@@ -257,7 +295,10 @@ class Server:
             else:
                 j.future.set_exception(err)
             at += j.n
+        held = self.ctx.bytes()   # a call may have grown its stream's workspace beyond the reservation
         with self.lock:
+            self.ws_cap[u.slot] += held - self.ws_bytes
+            self.ws_bytes = held
             self.used -= u.bytes
             self.busy[u.slot] = False
             self.done.extend(u.jobs)
@@ -279,17 +320,18 @@ class Server:
                 for slot in range(len(self.streams)):
                     if self.busy[slot]:
                         continue
-                    jobs = self._take_unit()
-                    if jobs is None:
+                    picked = self._take_unit(slot)
+                    if picked is None:
                         break
+                    jobs, need = picked
                     self.busy[slot] = True
                     self.used += sum(j.device_bytes() for j in jobs)
-                    launches.append((jobs, slot))
+                    launches.append((jobs, slot, need))
                 if not launches and not self.inflight and not self.stop_flag:
                     self.wake.wait(timeout=0.01)
-            for jobs, slot in launches:
+            for jobs, slot, need in launches:
                 try:
-                    self.inflight.append(self._launch(jobs, slot))
+                    self.inflight.append(self._launch(jobs, slot, need))
                 except Exception as exc:
                     with self.lock:
                         self.busy[slot] = False

@@ -103,6 +103,31 @@ int main(int argc, char** argv) {
     for (int32_t k = 0; k < n; ++k)
         if (out[perm[k]] != n - 1 - k) return fail("lr_rank_host value");
 
+    /* a context: reserve a second stream's workspace up front, rank on it, free it */
+    {
+        lrcc_ctx* ctx = NULL;
+        cudaStream_t s2;
+        if (cudaStreamCreate(&s2) != cudaSuccess) return fail("second stream");
+        if (lrcc_ctx_create(&ctx, -1) != LRCC_ERR_ARG || ctx != NULL) return fail("bad device accepted");
+        if (lrcc_ctx_create(&ctx, 0) != LRCC_OK || ctx == NULL) return fail("lrcc_ctx_create");
+        if (lrcc_ctx_bytes(ctx) != 0) return fail("a new context holds bytes");
+        const int64_t need = lrcc_workspace_query(1, n, 0);
+        if (need < 0) return fail("lrcc_workspace_query");
+        if (lrcc_ctx_reserve(ctx, s2, need) != LRCC_OK) return fail("lrcc_ctx_reserve");
+        const int64_t held = lrcc_ctx_bytes(ctx);
+        if (held < need) return fail("reserved bytes not counted");
+        if (lr_rank(d_succ, n, perm[0], d_out, s2) != LRCC_OK) return fail("lr_rank on the reserved stream");
+        if (lrcc_ctx_last_status(ctx, s2) != LRCC_OK) return fail("context status after a valid list");
+        if (lrcc_ctx_bytes(ctx) != held) return fail("a call within the reservation grew the workspace");
+        if (cudaMemcpy(out, d_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return fail("copy out (ctx)");
+        for (int32_t k = 0; k < n; ++k)
+            if (out[perm[k]] != n - 1 - k) return fail("lr_rank value on the reserved stream");
+        if (lrcc_ctx_reserve(ctx, s2, -1) != LRCC_ERR_ARG) return fail("negative reservation accepted");
+        lrcc_ctx_destroy(ctx);
+        lrcc_ctx_destroy(NULL);
+        cudaStreamDestroy(s2);
+    }
+
     /* errors: argument errors return at once, input errors reach the status word */
     if (lr_rank(d_succ, n, n, d_out, s) != LRCC_ERR_ARG) return fail("head out of range accepted");
     if (lr_rank(NULL, n, 0, d_out, s) != LRCC_ERR_ARG) return fail("NULL input accepted");

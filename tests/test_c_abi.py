@@ -1,7 +1,8 @@
 """The boundary from plain C: `tests/c_abi/abi_check.c` includes only
 `include/lrcc.h` and the CUDA runtime, links liblrcc.so, and checks lr_rank,
-lr_rank_wyllie, cc_label and lr_rank_host against closed forms, plus the error
-paths. Compiling and linking it needs no GPU; running it does."""
+lr_rank_wyllie, cc_label and lr_rank_host against closed forms, a context
+(create, reserve a stream's workspace, rank on it, count, destroy), plus the
+error paths. Compiling and linking it needs no GPU; running it does."""
 from __future__ import annotations
 
 import os

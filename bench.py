@@ -43,7 +43,7 @@ LR_METHOD_NOTE = {
 
 # ncu DRAM bytes of one first-level walk launch (rs_walk0c) at n = 2^28, random
 # layout: dram__bytes_read.sum + dram__bytes_write.sum of a capture at n = 2^26
-# (7.577 GB + 0.425 GB; ncu of `profile_case lr 26 readonly`) scaled by the 4x elements,
+# (7.577 GB + 0.425 GB; ncu of `bench.py --case lr 26 readonly`) scaled by the 4x elements,
 # and the hash of the walk's source it was taken from. Reported only while that source is unchanged.
 NCU_WALK0 = {"walk_sha1": "c25e2ada6cb65213a46102a9c32609ea32aeb872", "bytes_per_launch": 4 * (7.576812e9 + 0.424543e9)}
 
@@ -69,7 +69,59 @@ def parse():
     ap.add_argument("--plain-launches", action="store_true",
                     help="launch kernels directly instead of replaying CUDA graphs (for profilers that cannot "
                          "see kernels inside graphs with conditional nodes)")
+    ap.add_argument("--case", nargs="+", metavar="ARG",
+                    help="run one library call on a seeded input for a profiler and exit: "
+                         "lr LOG2 [inplace|readonly|split] | wyllie LOG2 | cc SCALE | batch LOG2COUNT")
     return ap.parse_args()
+
+
+def run_case(argv):
+    """One call of the library on a seeded input, for profilers (ncu), with
+    plain launches so that the profiler sees every kernel; the result is checked
+    (the list's closed form, the component invariants) before it exits 0.
+
+        lr 26 [inplace|readonly|split]   lr_rank, random list of 2^26
+        wyllie 24                        lr_rank_wyllie
+        cc 22                            cc_label, R-MAT scale 22, edge factor 16
+        batch 10                         2^10 mixed instances, both batched calls
+    """
+    import torch
+    import gen
+    from gen import workloads
+    import paper_1002_4482_gb300 as lrcc
+    what, log2 = argv[0], int(argv[1])
+    variant = argv[2] if len(argv) > 2 else ""
+    dev = torch.device("cuda:0")
+    for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC, lrcc.KIND_LR_BATCH, lrcc.KIND_CC_BATCH):
+        lrcc.set_plan(kind, 0, 32, use_graphs=2)
+    level0 = {"inplace": 1, "readonly": 2, "split": 3}
+    if variant in level0:
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=level0[variant])
+    if what in ("lr", "wyllie"):
+        succ, head, perm = gen.list_random(1 << log2, 3, with_perm=True)
+        s = torch.from_numpy(succ).to(dev)
+        fn = lrcc.lr_rank if what == "lr" else lrcc.lr_rank_wyllie
+        rank = fn(s, head)
+        lrcc.check()
+        r = rank.cpu().numpy()
+        assert np.array_equal(r[perm], np.arange((1 << log2) - 1, -1, -1, dtype=np.int32))
+    elif what == "cc":
+        src, dst, n = workloads.cc_rmat(log2, 16)
+        lab = lrcc.cc_label(torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev), n)
+        lrcc.check()
+        lab = lab.cpu().numpy()
+        assert np.array_equal(lab[src], lab[dst]) and (lab <= np.arange(n)).all()
+        assert np.array_equal(lab[lab], lab)
+        log("rounds", lrcc.last_stats()["rounds"])
+    elif what == "batch":
+        (succ, off, heads), (src, dst, eoff, voff) = workloads.batch(1 << log2)
+        lrcc.lr_rank_batched(*(torch.from_numpy(x).to(dev) for x in (succ, off, heads)))
+        lrcc.cc_label_batched(*(torch.from_numpy(x).to(dev) for x in (src, dst, eoff, voff)))
+        lrcc.check()
+    else:
+        raise SystemExit(f"unknown case {what}")
+    torch.cuda.synchronize()
+    log("ok", what, log2, variant)
 
 
 def workload(name):
@@ -349,12 +401,22 @@ def bench_families(lrcc, torch, dev, stream, m=8_000_000):
     return out
 
 
-def bench_batched(lrcc, torch, dev, stream, log2_count=12):
+def bench_batched(lrcc, torch, dev, stream, log2_count=12, world=1, rank_id=0, max_fn=None):
     """4096 instances (2048 lists + 2048 graphs of average degree 4, sizes
     log-uniform in [2^8, 2^20)): one batched launch per kind against one
-    launch per instance on the same stream, and spread over 8 streams."""
+    launch per instance on the same stream, and spread over 8 streams. With
+    several ranks the instances are shared out by LPT (shard.py) and every rank
+    runs one batched launch per kind on its share; the time is the slowest
+    rank's (the per-instance comparison runs alone only)."""
     from gen import workloads
+    from paper_1002_4482_gb300 import shard
     (succ, off, heads), (src, dst, eoff, voff) = workloads.batch(1 << log2_count)
+    all_units = len(succ) + len(src)
+    if world > 1:
+        li = shard.lpt_assign(shard.list_costs(off), world)[rank_id]
+        gi = shard.lpt_assign(shard.graph_costs(eoff, voff), world)[rank_id]
+        succ, off, heads = shard.list_share(succ, off, heads, li)
+        src, dst, eoff, voff = shard.graph_share(src, dst, eoff, voff, gi)
     with torch.cuda.stream(stream):
         S, O, H = (torch.from_numpy(x).to(dev) for x in (succ, off, heads))
         SR, DS, EO, VO = (torch.from_numpy(x).to(dev) for x in (src, dst, eoff, voff))
@@ -376,6 +438,13 @@ def bench_batched(lrcc, torch, dev, stream, log2_count=12):
 
     lr_b = ev(lambda: lrcc.lr_rank_batched(S, O, H, out=rank, stream=stream), 3)
     cc_b = ev(lambda: lrcc.cc_label_batched(SR, DS, EO, VO, n_total=int(voff[-1]), out=lab, stream=stream), 3)
+    if world > 1:
+        slowest = max_fn(lr_b + cc_b)
+        return {"workload": "2048 lists + 2048 graphs (avg degree 4), sizes log-uniform [2^8, 2^20), int64 offsets; "
+                            f"instances shared out over {world} ranks by LPT, one batched launch per kind per rank",
+                "ranks": world, "rank0_instances": {"lists": int(len(heads)), "graphs": int(len(voff) - 1)},
+                "rank0_batched_ms": {"lr": lr_b, "cc": cc_b}, "slowest_rank_ms": slowest,
+                "batched_melems_per_s": all_units / slowest / 1e3}
     offs, hs, eo, vo = off.tolist(), heads.tolist(), eoff.tolist(), voff.tolist()
 
     def per_lr():
@@ -486,6 +555,9 @@ def bench_serve(torch, count=400, seed=6):
 
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     if args.warmup < 3:
         log("warmup raised to 3")
         args.warmup = 3
@@ -801,10 +873,11 @@ def main():
     if rank == 0 and not args.no_sweep:
         sweep = bench_lr_sweep(lrcc, torch, dev, stream, (16, 18, 20, 22, 24, 26, 28) if args.workload == "large"
                                else (12, 14, 16, 18, 20))
-    if rank == 0 and not args.no_batched:
+    if not args.no_batched:
         del rank_out, label, src, dst, succ
         torch.cuda.empty_cache()
-        batched = bench_batched(lrcc, torch, dev, stream)
+        barrier()
+        batched = bench_batched(lrcc, torch, dev, stream, world=world, rank_id=rank, max_fn=max_over_ranks)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_serve:
         serving = bench_serve(torch, args.serve_jobs)

@@ -189,3 +189,25 @@ def test_large_batch_with_the_in_place_plan_takes_the_block_path():
     finally:
         lrcc.reset_plans()
     assert np.array_equal(rank.cpu().numpy(), oracle.lr_rank_batched(succ, off, heads))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_shares_gather_to_the_whole_batch(world):
+    # the batched calls on each rank's LPT share (run here one share after the
+    # other on one GPU), put back in place: equal to the oracle on the whole batch
+    from paper_1002_4482_gb300 import shard
+    (succ, off, heads), (src, dst, eoff, voff) = workloads.batch(256, 6.0, 17.0, seed=21)
+    rank_all = np.full(len(succ), -9, np.int32)
+    lab_all = np.full(int(voff[-1]), -9, np.int32)
+    for idx in shard.lpt_assign(shard.list_costs(off), world):
+        s, o, h = shard.list_share(succ, off, heads, idx)
+        r = lrcc.lr_rank_batched(*(torch.from_numpy(x).to(DEV) for x in (s, o, h)))
+        lrcc.check()
+        shard.scatter_back(rank_all, off, idx, r.cpu().numpy())
+    for idx in shard.lpt_assign(shard.graph_costs(eoff, voff), world):
+        a, b, eo, vo = shard.graph_share(src, dst, eoff, voff, idx)
+        lab = lrcc.cc_label_batched(*(torch.from_numpy(x).to(DEV) for x in (a, b, eo, vo)))
+        lrcc.check()
+        shard.scatter_back(lab_all, voff, idx, lab.cpu().numpy())
+    assert np.array_equal(rank_all, oracle.lr_rank_batched(succ, off, heads))
+    assert np.array_equal(lab_all, oracle.cc_batched(src, dst, eoff, voff))

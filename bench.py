@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-families", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the list-ranking size sweep")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=400)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--plain-launches", action="store_true",
                     help="launch kernels directly instead of replaying CUDA graphs (for profilers that cannot "
                          "see kernels inside graphs with conditional nodes)")
@@ -352,6 +352,124 @@ def bench_lr_sweep(lrcc, torch, dev, stream, sizes=(16, 18, 20, 22, 24, 26, 28))
     return out
 
 
+def bench_small_configs(lrcc, torch, dev, stream, hbm, reps=20):
+    """The two small configurations as legs of their own: list ranking of a
+    2^20-element random list, and components of a uniform random graph with
+    2^20 vertices and 2^22 edges. Both fit in L2, so a 256 MB buffer is written
+    between timed calls (L2 flushed); each call is timed alone with CUDA events
+    on the launching stream, median of `reps`. The oracle runs on the same full
+    inputs on one host core."""
+    import oracle
+    from gen import workloads
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        fn()
+        stream.synchronize()
+        ts = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        lrcc.check(stream)
+        ts.sort()
+        return ts[len(ts) // 2], ts[0]
+
+    out = {}
+    succ_h, head = workloads.lr_random(20)
+    n = len(succ_h)
+    with torch.cuda.stream(stream):
+        s_d = torch.from_numpy(succ_h).to(dev)
+        r_d = torch.empty_like(s_d)
+    med, best = timed(lambda: lrcc.lr_rank(s_d, head, out=r_d, stream=stream))
+    t0 = time.perf_counter()
+    want = oracle.lr_rank(succ_h, head)
+    t_cpu = time.perf_counter() - t0
+    assert np.array_equal(r_d.cpu().numpy(), want)
+    out["lr_random_2p20"] = {
+        "metric": "Mnodes/s", "value": n / med / 1e3, "ms_median": med, "ms_min": best,
+        "roofline": {"bound": "hbm", "achieved": 8 * n / (med / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": 8 * n / (med / 1e3) / 1e9 / hbm, "traffic": None,
+                     "note": "problem bytes (4 B succ read + 4 B rank written per element) over the whole call; "
+                             "the 4 MB list is launch- and latency-bound"},
+        "cpu_baseline": {"value": n / t_cpu / 1e6, "unit": "Mnodes/s", "cores": 1, "kind": "oracle",
+                         "sample": "the same 2^20-element list, whole"}}
+    src_h, dst_h, nv = workloads.cc_er(20, 22)
+    m = len(src_h)
+    with torch.cuda.stream(stream):
+        a_d = torch.from_numpy(src_h).to(dev)
+        b_d = torch.from_numpy(dst_h).to(dev)
+        l_d = torch.empty(nv, dtype=torch.int32, device=dev)
+    med, best = timed(lambda: lrcc.cc_label(a_d, b_d, nv, out=l_d, stream=stream))
+    t0 = time.perf_counter()
+    want = oracle.cc_uf(src_h, dst_h, nv)
+    t_cpu = time.perf_counter() - t0
+    assert np.array_equal(l_d.cpu().numpy(), want)
+    pbytes = 8 * m + 4 * nv
+    out["cc_er_2p20_2p22"] = {
+        "metric": "Medges/s", "value": m / med / 1e3, "ms_median": med, "ms_min": best,
+        "rounds": lrcc.last_stats(stream)["rounds"],
+        "roofline": {"bound": "hbm", "achieved": pbytes / (med / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": pbytes / (med / 1e3) / 1e9 / hbm, "traffic": None,
+                     "note": "problem bytes (8 B per edge read, 4 B per label written) over the whole call"},
+        "cpu_baseline": {"value": m / t_cpu / 1e6, "unit": "Medges/s", "cores": 1, "kind": "oracle",
+                         "sample": "the same graph, whole (union-find)"}}
+    del flush, s_d, r_d, a_d, b_d, l_d
+    return out
+
+
+def bench_even_splitters(lrcc, torch, dev, stream, sizes=(16, 20, 24, 28)):
+    """The paper's Table 3 on GB300 (Sec. 3.2): the same random-layout list
+    ranked with random splitters and with a perfect set of even splitters (list
+    positions 0, D, 2D, ...: every sublist exactly D elements), both through the
+    in-place first level at the plan's spacing D."""
+    import gen
+    out = []
+    base = {k: lrcc.get_plan(lrcc.KIND_LR, 1 << k) for k in sizes}
+
+    def best_ms(fn):
+        fn()
+        stream.synchronize()
+        best = float("inf")
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        lrcc.check(stream)
+        return best
+
+    try:
+        for lg in sizes:
+            n = 1 << lg
+            D = base[lg]["rs_spacing0"]
+            succ_h, head, perm = gen.list_random(n, 100 + lg, with_perm=True)
+            with torch.cuda.stream(stream):
+                s_d = torch.from_numpy(succ_h).to(dev)
+                r_d = torch.empty_like(s_d)
+                even = torch.from_numpy(np.ascontiguousarray(perm[::D])).to(dev)
+            lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=1)
+            t_rand = best_ms(lambda: lrcc.lr_rank(s_d, head, out=r_d, stream=stream))
+            t_even = best_ms(lambda: lrcc.lr_rank_splitters(s_d, head, even, out=r_d, stream=stream))
+            if int(r_d[head].item()) != n - 1:
+                raise AssertionError("even splitters gave a wrong head rank")
+            out.append({"log2n": lg, "spacing": D, "random_ms": t_rand, "even_ms": t_even,
+                        "random_gnodes_per_s": n / t_rand / 1e6, "even_gnodes_per_s": n / t_even / 1e6,
+                        "even_speedup": t_rand / t_even})
+            del s_d, r_d, even
+    finally:
+        for lg in sizes:
+            lrcc.set_plan(lrcc.KIND_LR, lg, lg, rs_level0=base[lg]["rs_level0"])
+    return out
+
+
 def bench_families(lrcc, torch, dev, stream, m=8_000_000):
     """The paper's component families (Sec. 4): collections of random lists, random
     trees of degree k and random graphs of edge density d, all with m edges; hook
@@ -499,16 +617,19 @@ def bench_batched(lrcc, torch, dev, stream, log2_count=12, world=1, rank_id=0, m
             "batched_melems_per_s": units / (lr_b + cc_b) / 1e3}
 
 
-def bench_serve(torch, count=400, seed=6):
+def bench_serve(torch, count=2000, seed=6, loads=(0.5, 0.8, 0.95), repeats=3):
     """Poisson stream of mixed jobs (70 % lists / 30 % graphs of average
     degree 8, sizes log-uniform in [2^10, 2^24)) through the continuous-
     batching server and through one-launch-per-job FIFO: saturated (all
-    submitted at once) and at half the saturated rate."""
-    import threading
+    submitted at once) and at offered loads of 0.5, 0.8 and 0.95 times the
+    batched server's saturated rate; every run `repeats` times, reported as the
+    median with the range."""
     import gen
     from gen import workloads
     from paper_1002_4482_gb300 import serve
-    grid = np.unique(np.floor(2.0 ** np.arange(10, 24.01, 0.25)).astype(np.int64))
+    # inputs come from a pool of seeded instances on an 8-per-octave size grid
+    # (a job's size is rounded down to the grid), so the host builds them in seconds
+    grid = np.unique(np.floor(2.0 ** np.arange(10, 24.01, 0.125)).astype(np.int64))
     _, kind, size = workloads.serve_jobs(count, 1.0, seed=seed)
     pool = {}
 
@@ -540,17 +661,33 @@ def bench_serve(torch, count=400, seed=6):
         srv.close()
         return st
 
-    out = {"workload": f"{count} jobs: 70 % lists / 30 % graphs (degree 8), sizes log-uniform [2^10, 2^24); "
-                       "inputs from a pool of seeded instances on a 4-per-octave size grid",
-           "saturated": {}, "half_load": {}}
-    out["saturated"]["batched"] = run(serve.Server(0, streams=4), np.zeros(count))
-    out["saturated"]["fifo"] = run(serve.FifoServer(0), np.zeros(count))
-    lam = 0.5 * out["saturated"]["batched"]["jobs_per_s"]
-    gaps = np.random.default_rng(seed).exponential(1.0 / lam, count)
-    out["half_load"]["offered_jobs_per_s"] = lam
-    out["half_load"]["batched"] = run(serve.Server(0, streams=4), gaps)
-    out["half_load"]["fifo"] = run(serve.FifoServer(0), gaps)
-    return out
+    def summary(runs):
+        out = {}
+        for key in ("p50_ms", "p99_ms", "jobs_per_s"):
+            v = sorted(r[key] for r in runs)
+            out[key] = v[len(v) // 2]
+            out[key + "_range"] = [v[0], v[-1]]
+        return out
+
+    res = {"workload": f"{count} jobs per run: 70 % lists / 30 % graphs (degree 8), sizes log-uniform [2^10, 2^24) "
+                       "rounded down to an 8-per-octave grid of seeded pooled instances",
+           "repeats": repeats, "saturated": {}, "loads": {}}
+    sat = {"batched": [], "fifo": []}
+    for _ in range(repeats):
+        sat["batched"].append(run(serve.Server(0, streams=4), np.zeros(count)))
+        sat["fifo"].append(run(serve.FifoServer(0), np.zeros(count)))
+    res["saturated"] = {k: summary(v) for k, v in sat.items()}
+    lam_sat = res["saturated"]["batched"]["jobs_per_s"]
+    for load in loads:
+        lam = load * lam_sat
+        row = {"offered_jobs_per_s": lam, "batched": [], "fifo": []}
+        for r in range(repeats):
+            gaps = np.random.default_rng(seed * 100 + r).exponential(1.0 / lam, count)
+            row["batched"].append(run(serve.Server(0, streams=4), gaps))
+            row["fifo"].append(run(serve.FifoServer(0), gaps))
+        res["loads"][str(load)] = {"offered_jobs_per_s": lam, "batched": summary(row["batched"]),
+                                   "fifo": summary(row["fifo"])}
+    return res
 
 
 def main():
@@ -673,6 +810,20 @@ def main():
     lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
     cc_stats = lrcc.last_stats(stream)
     lrcc.check(stream)
+
+    # the components' ceiling: the hook pass's edge stream and two parent gathers
+    # per edge without the hooking (lrcc_gather_probe over the same edges and a
+    # table the size of the parent array), timed like the step
+    with torch.cuda.stream(stream):
+        lrcc.gather_probe(src, dst, label, stream=stream)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(3):
+            lrcc.gather_probe(src, dst, label, stream=stream)
+        p1.record(stream)
+    stream.synchronize()
+    lrcc.check(stream)
+    probe_ms = p0.elapsed_time(p1) / 3
 
     lr_ms = sum(v[0] for k, v in phases.items() if k.startswith(("rs_", "lr_small"))) / args.steps
     cc_ms = sum(v[0] for k, v in phases.items() if k.startswith("cc_")) / args.steps
@@ -870,6 +1021,13 @@ def main():
     families = sweep = None
     if rank == 0 and not args.no_families:
         families = bench_families(lrcc, torch, dev, stream)
+    even = None
+    small = None
+    if rank == 0 and args.workload == "large":
+        small = bench_small_configs(lrcc, torch, dev, stream, hbm)
+    if rank == 0 and not args.no_sweep:
+        even = bench_even_splitters(lrcc, torch, dev, stream, (16, 20, 24, 28) if args.workload == "large"
+                                    else (12, 16, 20))
     if rank == 0 and not args.no_sweep:
         sweep = bench_lr_sweep(lrcc, torch, dev, stream, (16, 18, 20, 22, 24, 26, 28) if args.workload == "large"
                                else (12, 14, 16, 18, 20))
@@ -911,9 +1069,18 @@ def main():
                        "method_bytes_frac": cc_method / (cc_ms / 1e3) / 1e9 / hbm if cc_ms else None,
                        "method_bytes_note": "16 B per edge read by a hook pass (8 B of edge, two 4-byte parent "
                                             "gathers), 8 B per vertex and shortcut pass, 4 B per vertex of init; "
-                                            "R = rounds"},
+                                            "R = rounds",
+                       "gather_ceiling": {
+                           "probe_ms_per_pass": probe_ms, "probe_gedges_per_s": m_cc / probe_ms / 1e6,
+                           "edges_read": cc_stats["edges_read"],
+                           "ceiling_ms": cc_stats["edges_read"] / (m_cc / probe_ms),
+                           "frac": (cc_stats["edges_read"] / (m_cc / probe_ms)) / cc_ms if cc_ms else None,
+                           "note": "probe: the hook pass's 16-byte edge stream and two gathers per edge (L1, "
+                                   "evict-last) over a 4n-byte table, no hooking (lrcc_gather_probe); ceiling: "
+                                   "every edge the hook passes read, at the probe's rate; frac = ceiling / cc ms"}},
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
                 "batched": batched, "serving": serving, "cc_families": families, "lr_sweep": sweep,
+                "even_vs_random_splitters": even, "small_configs": small,
                 **extra}
         print(json.dumps(line), flush=True)
     ranks.shutdown()

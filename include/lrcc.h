@@ -78,6 +78,27 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
 lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream);
 
 /*
+ * List ranking with the first-level splitters chosen by the caller: the
+ * paper's comparison of random splitters with a perfect set of even splitters
+ * that cut the list into sublists of equal length (Sec. 3.2, Table 3).
+ *
+ *   succ, n, head, rank   as for lr_rank
+ *   spl   int32[r]        device array of distinct element ids; spl[0] must be
+ *                         head; spl[j] becomes splitter j
+ *   r                     1 <= r <= n
+ *
+ * The first level is the in-place one (64-bit words, plan rs_level0 = 1),
+ * whose packed words carry the splitter marks, so the given splitters cost
+ * the walk nothing extra; the deeper levels choose their splitters as
+ * lr_rank does. Lists of at most the plan's rs_small elements are ranked in
+ * one block and do not use spl. An id out of range, an id given twice or
+ * spl[0] != head records LRCC_ERR_INVALID_INPUT. The ranks do not depend on
+ * the splitters.
+ */
+lrcc_status lr_rank_splitters(const int32_t* succ, int64_t n, int32_t head, const int32_t* spl, int64_t r,
+                              int32_t* rank, void* stream);
+
+/*
  * List ranking for callers that cannot allocate device memory: code whose
  * device memory is fixed up front (a framework that owns the allocator, a
  * service that only uses memory reserved at start-up, a loop where a
@@ -86,9 +107,13 @@ lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t
  *
  * Same arguments as lr_rank, with n <= 2^20 (larger n returns LRCC_ERR_ARG
  * at once). The call allocates nothing. Its scratch (about 10 MiB) is held by
- * every GPU that loads the library, until the process exits; the first call
- * on each device looks up the array's device address (cudaGetSymbolAddress)
- * and should be made before any stream capture. All calls on a device share
+ * a GPU until the process exits; the first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) and should be made before any
+ * stream capture. Under CUDA's default lazy module loading that lookup is what
+ * loads the library's device code onto the device, so the 10 MiB are committed
+ * during the first call on each device (which can then fail for lack of
+ * memory), not when the library is loaded: make one warm-up call per device
+ * during set-up, or run with CUDA_MODULE_LOADING=EAGER. All calls on a device share
  * the array, so calls whose work overlaps on the GPU race: order them (one
  * stream). An input that is not a single list sets rank[head] = -1 (the
  * stream's status word is not used). Returns LRCC_ERR_ARG while phase timing
@@ -224,6 +249,18 @@ lrcc_status lrcc_last_status(void* stream);
  * nothing beyond the stream's status word.
  */
 lrcc_status lrcc_wait_check(int polls, void* stream);
+
+/*
+ * Measurement aid: the memory traffic of one components hook pass without its
+ * work. Streams the edge list (src, dst: int32[m], device) as the hook pass
+ * does and gathers table[src[e]] and table[dst[e]] for every edge from a
+ * device table of n int32 (the parent array's size and cache policy); the
+ * wrapped sum of the gathered values goes to *out (a device int64), so no
+ * load is dropped. Ids outside [0, n) gather entry 0. Asynchronous on
+ * `stream`; allocates nothing beyond the stream's status word.
+ */
+lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m, const int32_t* table, int64_t n,
+                              int64_t* out, void* stream);
 
 /* Statistics of the most recent call on `stream` (waits for the stream). */
 typedef struct lrcc_stats {

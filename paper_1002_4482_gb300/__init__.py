@@ -35,7 +35,8 @@ SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_r
            "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans", "lrcc_release", "lrcc_workspace_bytes",
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity",
-           "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_bytes", "lrcc_ctx_last_status", "lrcc_ctx_destroy")
+           "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_bytes", "lrcc_ctx_last_status", "lrcc_ctx_destroy",
+           "lrcc_gather_probe", "lr_rank_splitters")
 
 
 class LrccError(RuntimeError):
@@ -111,6 +112,8 @@ def load() -> ctypes.CDLL:
         lib.lrcc_ctx_last_status.argtypes = [p, p]
         lib.lrcc_ctx_destroy.argtypes = [p]
         lib.lrcc_ctx_destroy.restype = None
+        lib.lrcc_gather_probe.argtypes = [p, p, i64, p, i64, p, p]
+        lib.lr_rank_splitters.argtypes = [p, i64, i32, p, i64, p, p]
         for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_host", "cc_label_host",
                   "lr_scan", "lr_scan_forest",
                   "lr_rank_batched",
@@ -118,7 +121,8 @@ def load() -> ctypes.CDLL:
                   "cc_label_batched", "cc_label_batched_sized",
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity",
-                  "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_last_status"):
+                  "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_last_status", "lrcc_gather_probe",
+                  "lr_rank_splitters"):
             getattr(lib, f).restype = i
         _lib = lib
         return lib
@@ -195,6 +199,18 @@ def lr_rank_wyllie(succ: torch.Tensor, head: int, out: torch.Tensor | None = Non
     rank = _out(out, succ.numel(), succ, "out")
     _call(load().lr_rank_wyllie(succ.data_ptr(), succ.numel(), int(head), rank.data_ptr(), _stream(stream)),
           "lr_rank_wyllie")
+    return rank
+
+
+def lr_rank_splitters(succ: torch.Tensor, head: int, spl: torch.Tensor, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Same result as :func:`lr_rank`, with the first-level splitters given
+    (spl[0] = head; the paper's even-splitter comparison, Sec. 3.2)."""
+    _dev_i32(succ, "succ")
+    _dev_i32(spl, "spl")
+    rank = _out(out, succ.numel(), succ, "out")
+    _call(load().lr_rank_splitters(succ.data_ptr(), succ.numel(), int(head), spl.data_ptr(), spl.numel(),
+                                   rank.data_ptr(), _stream(stream)), "lr_rank_splitters")
     return rank
 
 
@@ -367,6 +383,19 @@ def workspace_bytes() -> int:
 
 def workspace_query(kind: int, n: int, m: int = 0) -> int:
     return int(load().lrcc_workspace_query(kind, n, m))
+
+
+def gather_probe(src: torch.Tensor, dst: torch.Tensor, table: torch.Tensor, stream=None) -> torch.Tensor:
+    """The hook pass's edge stream and two gathers per edge from `table`, without
+    the hooking (lrcc_gather_probe): a ceiling for the pass. Returns the device
+    int64 sum of the gathered values."""
+    src = _dev_i32(src, "src")
+    dst = _dev_i32(dst, "dst")
+    table = _dev_i32(table, "table")
+    out = torch.zeros(1, dtype=torch.int64, device=table.device)
+    _call(load().lrcc_gather_probe(src.data_ptr(), dst.data_ptr(), src.numel(), table.data_ptr(), table.numel(),
+                                   out.data_ptr(), _stream(stream)), "lrcc_gather_probe")
+    return out
 
 
 def set_timing(enable: bool) -> None:

@@ -178,6 +178,49 @@ __global__ void __launch_bounds__(BLOCK, 6)
     if (__any_sync(0xffffffffu, changed) && lane == 0) ctl->flag = 1;
 }
 
+// Ceiling of a hook pass's memory traffic: the same edge stream (16-byte
+// evict-first loads) and the same two gathers per edge (through L1, evict-last
+// in L2) over a table the size of the parent array, with none of the hooking.
+// The gathered values are summed (one atomic per block) so that no load is
+// dropped.
+template <bool VEC>
+__global__ void __launch_bounds__(BLOCK, 6)
+    cc_gather_probe(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                    const int32_t* table, int64_t n, unsigned long long* out) {
+    const uint64_t stream_pol = policy_evict_first();
+    const uint64_t keep = policy_evict_last();
+    const int64_t ngroups = (m + 3) >> 2;
+    unsigned long long acc = 0;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; g < ngroups;
+         g += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int64_t e0 = g * 4;
+        int u[4], v[4];
+        if (VEC && e0 + 3 < m) {
+            const int4 a = ld_stream_v4(src + e0, stream_pol);
+            const int4 b = ld_stream_v4(dst + e0, stream_pol);
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+            v[0] = b.x; v[1] = b.y; v[2] = b.z; v[3] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                u[q] = e0 + q < m ? ld_stream(src + e0 + q, stream_pol) : 0;
+                v[q] = e0 + q < m ? ld_stream(dst + e0 + q, stream_pol) : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (e0 + q >= m) continue;
+            // ids outside [0, n) read entry 0 instead (the probe never faults)
+            const int uq = (u[q] >= 0 && u[q] < n) ? u[q] : 0;
+            const int vq = (v[q] >= 0 && v[q] < n) ? v[q] : 0;
+            acc += (unsigned)ld_hint(table + uq, keep) + (unsigned)ld_hint(table + vq, keep);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 // Pointer jumping to stars: parent[v] <- root(v). Roots do not move during
 // this pass and every value read is an ancestor, so one pass suffices.
 template <bool VEC>
@@ -369,6 +412,20 @@ lrcc_status build_loop_graph(Ctx* c, const CcArgs& a, cudaGraphExec_t* out) {
 }
 
 }  // namespace
+
+lrcc_status cc_gather_probe_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, const int32_t* table,
+                                int64_t n, int64_t* out) {
+    const bool ve = aligned16(src) && aligned16(dst);
+    const void* k = ve ? (const void*)cc_gather_probe<true> : (const void*)cc_gather_probe<false>;
+    const int64_t eg = (m + 3) / 4;
+    cudaMemsetAsync(out, 0, sizeof(int64_t), c->stream);
+    if (eg == 0) return cuda_status(cudaGetLastError());
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((eg + BLOCK - 1) / BLOCK, persistent_grid(c, k, BLOCK)));
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
+    if (ve) cc_gather_probe<true><<<g, BLOCK, 0, c->stream>>>(src, dst, m, table, n, o);
+    else cc_gather_probe<false><<<g, BLOCK, 0, c->stream>>>(src, dst, m, table, n, o);
+    return cuda_status(cudaGetLastError());
+}
 
 // Active-edge buffers: each holds an eighth of the edges (a pass that keeps
 // more falls back to the full edge list); none for small graphs.

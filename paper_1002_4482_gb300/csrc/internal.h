@@ -51,12 +51,18 @@ struct RsLayout {
     bool split = false;             // level 0 over split mark / local-rank arrays
     int64_t grid = 0, cap = 0, ovf_cap = 0;
     int segcap = 0, units = 0;
+    int nb_log = 8;                 // coarse id buckets of the scatter: 2^nb_log
     size_t off_ids = 0, off_meta = 0, off_fill = 0, off_counts = 0, off_totals = 0,
         off_vis = 0;
+    // placement through shared-memory windows (read-only level 0)
+    bool pw = false;
+    int pw_fw_log = 0, pw_clusters = 0, pw_ntile = 0;
+    size_t off_pw_scratch = 0, off_pw_hdr = 0;
     size_t bytes = 0;
 };
 // extra1: extra first-level splitters (the heads of batched lists ranked as one list)
-RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1 = 0);
+// given1: the number of first-level splitters when the caller chooses them
+RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1 = 0, int64_t given1 = 0);
 
 // Batched lists ranked as one list by the read-only first level: K lists own
 // [off[k], off[k+1]) of succ with local ids; device scratch for the global
@@ -141,7 +147,7 @@ int persistent_grid(Ctx* c, const void* kernel, int block, size_t smem = 0);
 // needs the in-place first level (L.readonly false).
 lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
                           int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val = nullptr,
-                          const BatchUnion* U = nullptr);
+                          const BatchUnion* U = nullptr, const int32_t* given = nullptr, int64_t given_r = 0);
 // Weighted ranks of a forest of lists (ruling set with the heads as extra
 // splitters; pointer jumping when the values rule that out).
 size_t lr_scan_forest_ws(int64_t n, const Plan& p);
@@ -156,6 +162,9 @@ size_t lr_wyllie_ws(int64_t n, const Plan& p);
 lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
                    int32_t* label, const Plan& p);
 int64_t cc_active_cap(int64_t m);
+// The hook pass's edge stream and parent gathers without the hooking (a ceiling).
+lrcc_status cc_gather_probe_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, const int32_t* table,
+                                int64_t n, int64_t* out);
 size_t cc_ws(int64_t m);
 // The Shiloach-Vishkin round structure (plan.cc_hook = 4): workspace, run, round bound.
 size_t cc_sv_ws(int64_t n);

@@ -16,6 +16,8 @@
 // the tail, itself included); the final rank is S - 1.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "block_wyllie.cuh"
@@ -124,7 +126,7 @@ template <bool VEC>
 __global__ void __launch_bounds__(BLOCK)
     rs_select0(const int32_t* __restrict__ succ, const int32_t* __restrict__ val, int64_t n, int32_t head,
                uint64_t* __restrict__ W, int32_t* __restrict__ snext, int32_t* __restrict__ sw, int logD,
-               int64_t nb, uint32_t seed, DevCtl* ctl) {
+               int64_t nb, uint32_t seed, DevCtl* ctl, bool mark = true) {
     if (ctl->scan_bad) return;
     const uint64_t pol = policy_evict_first();
     const int64_t D = int64_t(1) << logD;
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(BLOCK)
             const bool bad = !tail && (v < 0 || v >= n);
             if (i < n && bad) record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)i);
             const uint32_t nx = (tail || bad) ? NIL : (uint32_t)v;
-            if (i < n && (uint32_t)(i - (b << logD)) == off) {
+            if (mark && i < n && (uint32_t)(i - (b << logD)) == off) {
                 w[q] = pack(nx | SPL, (uint32_t)j);
                 snext[j] = (int32_t)nx;
                 sw[j] = wt[q];
@@ -179,6 +181,37 @@ __global__ void __launch_bounds__(BLOCK)
             for (int q = 0; q < 4; ++q)
                 if (i0 + q < n) W[i0 + q] = w[q];
         }
+    }
+}
+
+// First-level splitters given by the caller (the even-splitter experiment of
+// Sec. 3.2): spl[j] becomes splitter j of the words rs_select0 packed without
+// splitters. spl[0] must be the head; an element out of range or given twice
+// is reported (the first mark wins; the second finds SPL already set).
+__global__ void __launch_bounds__(BLOCK)
+    rs_mark_given(uint64_t* __restrict__ W, int64_t n, int32_t head, const int32_t* __restrict__ spl, int64_t r,
+                  int32_t* __restrict__ snext, int32_t* __restrict__ sw, DevCtl* ctl) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * BLOCK + threadIdx.x; j < r;
+         j += static_cast<int64_t>(gridDim.x) * BLOCK) {
+        const int32_t x = spl[j];
+        if (x < 0 || x >= n || (j == 0 && x != head)) {
+            record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)j);
+            snext[j] = (int32_t)NIL;
+            sw[j] = 0;
+            continue;
+        }
+        unsigned int* lo = reinterpret_cast<unsigned int*>(W + x);   // low word of the element's packed word
+        const unsigned int old = atomicOr(lo, SPL);
+        if (old & SPL) {
+            record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)j);
+            snext[j] = (int32_t)NIL;
+            sw[j] = 0;
+            continue;
+        }
+        const unsigned int weight = reinterpret_cast<const unsigned int*>(W + x)[1];
+        reinterpret_cast<unsigned int*>(W + x)[1] = (unsigned int)j;
+        snext[j] = (int32_t)old;
+        sw[j] = (int32_t)weight;
     }
 }
 
@@ -315,8 +348,12 @@ __global__ void __launch_bounds__(BLOCK)
 // splitter cannot trap it; valid lists never repeat an element.
 
 constexpr int CIDS = 8;        // element ids per chunk (one 32-byte sector)
-constexpr int NBK_LOG = 8;
-constexpr int NBK = 1 << NBK_LOG;
+// Coarse id buckets: 2^8 up to lists of 2^26 elements, then 2^(lg - 18) so that
+// one bucket holds at most 2^18 ids (the reach of one placement cluster), at
+// most 2^10.
+constexpr int NBK_LOG_MIN = 8;
+constexpr int NBK_LOG_MAX = 10;
+constexpr int NBK_MAX = 1 << NBK_LOG_MAX;
 constexpr int NSEG = 4;        // scatter work units per walk block region
 
 struct Level0 {
@@ -336,8 +373,8 @@ struct Chunks {
     int32_t* ids;        // chunk c: ids[8c .. 8c+8), unused slots -1
     uint64_t* meta;      // meta[c] = k0 << 32 | j
     int* fill;           // chunks written into each block's own region
-    int* counts;         // [NBK][units] elements per (bucket, scatter unit); then row offsets
-    int* totals;         // [NBK] elements per bucket
+    int* counts;         // [nb][units] elements per (bucket, scatter unit); then row offsets
+    int* totals;         // [nb] elements per bucket
     uint32_t* vis;       // careful-mode marks, one bit per element
     int64_t cap;         // chunks per block region (NSEG segments of segcap)
     int segcap;          // chunks per segment (even); a segment is one scatter work unit
@@ -345,6 +382,7 @@ struct Chunks {
     int64_t ovf_cap;     // overflow chunks
     int64_t ovf_base;    // index of the first overflow chunk (= grid * cap)
     int shift;           // coarse bucket of element x = x >> shift
+    int nb;              // coarse buckets (2^NBK_LOG_MIN .. NBK_MAX)
     int64_t careful;     // steps after which a walk marks what it visits
 };
 
@@ -383,8 +421,8 @@ __global__ void __launch_bounds__(BLOCK)
     }
     constexpr int WCHUNK = 64;
     __shared__ int s_fill;
-    __shared__ int s_cnt[NSEG][NBK];
-    for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) (&s_cnt[0][0])[t] = 0;
+    __shared__ int s_cnt[NSEG * NBK_MAX];   // [segment][bucket], nb buckets per segment
+    for (int t = threadIdx.x; t < NSEG * C.nb; t += BLOCK) s_cnt[t] = 0;
     if (threadIdx.x == 0) s_fill = 0;
     __syncthreads();
     const int64_t r = L0.nb + (L0.extra_count ? *L0.extra_count : 0);
@@ -499,7 +537,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
                     for (int t = 0; t < CIDS; ++t)
                         if (t < bn[q]) {
-                            if (ovf_unit < 0) atomicAdd(&s_cnt[seg][v[t] >> C.shift], 1);
+                            if (ovf_unit < 0) atomicAdd(&s_cnt[seg * C.nb + (v[t] >> C.shift)], 1);
                             else atomicAdd(&C.counts[(int64_t)(v[t] >> C.shift) * C.units + ovf_unit], 1);
                         }
                 }
@@ -517,15 +555,15 @@ __global__ void __launch_bounds__(BLOCK)
     }
     __syncthreads();
     if (threadIdx.x == 0) C.fill[blockIdx.x] = min(s_fill, (int)C.cap);
-    for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) {
-        const int bk = t % NBK, seg = t / NBK;
-        C.counts[(int64_t)bk * C.units + (int64_t)blockIdx.x * NSEG + seg] = s_cnt[seg][bk];
+    for (int t = threadIdx.x; t < NSEG * C.nb; t += BLOCK) {
+        const int bk = t % C.nb, seg = t / C.nb;
+        C.counts[(int64_t)bk * C.units + (int64_t)blockIdx.x * NSEG + seg] = s_cnt[t];
     }
 }
 
 // Exclusive scan of each bucket's row of per-block counts, in place, one
 // block per bucket; the row total goes to totals[bucket]. The start of each
-// bucket (a scan over NBK totals) is formed by the scatter blocks themselves.
+// bucket (a scan over the nb totals) is formed by the scatter blocks themselves.
 constexpr int SCAN_THREADS = 256;
 __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int G, int* totals) {
     __shared__ int s_warp[SCAN_THREADS / 32];
@@ -580,19 +618,19 @@ constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
 // open suspends the thread for a few microseconds (about 4.3 us measured on
 // GB300), so the limit is about one second.
 constexpr int SC_WAIT_LIMIT = 1 << 18;
+template <int NB>
 struct ScatterSmem {
     int32_t ids[SC_BUF][SC_ITEMS];      // chunk ids of the round in each buffer
     uint64_t meta[SC_BUF][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
     int32_t top[SC_CHUNKS];        // rank of the first element of each chunk
     uint16_t tile[SC_ITEMS];       // slot indices sorted by bucket
-    int cnt[2][NBK];               // elements per bucket in the round (alternating)
-    int base[NBK];                 // next free pair of each bucket for this region
-    int delta[NBK];                // pair position minus tile slot, per bucket, in the round
-    int tstart[NBK];               // start of each bucket's run in the tile
+    int cnt[2][NB];                // elements per bucket in the round (alternating)
+    int base[NB];                  // next free pair of each bucket for this region
+    int delta[NB];                 // pair position minus tile slot, per bucket, in the round
+    int tstart[NB];                // start of each bucket's run in the tile
     int warp[BLOCK / 32];
     uint64_t bar[SC_BUF];
 };
-constexpr size_t SC_SMEM = sizeof(ScatterSmem);
 
 // The 8 ids of one chunk from shared memory. Lanes 4-7 of every 8 read the
 // two 16-byte halves in the other order, so that each quarter-warp phase of
@@ -606,12 +644,15 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int32_t (&id)[CIDS]
     id[4] = hi.x; id[5] = hi.y; id[6] = hi.z; id[7] = hi.w;
 }
 
-__global__ void __launch_bounds__(BLOCK, 4)
+// NB buckets (C.nb == NB); thread t owns buckets [t * BPT, (t + 1) * BPT).
+template <int NB>
+__global__ void __launch_bounds__(BLOCK, NB <= 256 ? 4 : 3)
     rs_scatter(Chunks C, int G, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n,
                DevCtl* ctl) {
     extern __shared__ __align__(128) unsigned char sc_raw[];
-    ScatterSmem& s = *reinterpret_cast<ScatterSmem*>(sc_raw);
-    static_assert(NBK == BLOCK, "one thread per bucket");
+    ScatterSmem<NB>& s = *reinterpret_cast<ScatterSmem<NB>*>(sc_raw);
+    constexpr int BPT = NB / BLOCK;
+    static_assert(NB % BLOCK == 0, "whole buckets per thread");
     static_assert(SC_ITEMS <= 65536, "tile holds 16-bit slot indices");
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     // block-wide exclusive scan of one value per thread (uses s.warp; two syncs)
@@ -635,13 +676,21 @@ __global__ void __launch_bounds__(BLOCK, 4)
         *total = all;
         return off + incl - v;
     };
-    int bstart;                     // start of bucket t in the pair array
+    int bstart[BPT];                // start of each of this thread's buckets in the pair array
     {
-        int all = 0;
-        bstart = block_scan(C.totals[t], &all);
+        int all = 0, mine = 0;
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) mine += C.totals[t * BPT + k];
+        int at = block_scan(mine, &all);
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) {
+            bstart[k] = at;
+            at += C.totals[t * BPT + k];
+        }
         if (blockIdx.x == 0 && t == 0) ctl->pairs = all;
     }
-    s.cnt[0][t] = s.cnt[1][t] = 0;
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) s.cnt[0][t * BPT + k] = s.cnt[1][t * BPT + k] = 0;
     if (t == 0) {
         for (int b = 0; b < SC_BUF; ++b) mbar_init(&s.bar[b], 1);
         fence_proxy_async_smem();   // the initialised barriers are visible to the bulk copies
@@ -691,13 +740,23 @@ __global__ void __launch_bounds__(BLOCK, 4)
                 loc[u][q] = (c < cnt && id[q] >= 0) ? atomicAdd(&cntp[id[q] >> C.shift], 1) : 0;
         }
         __syncthreads();
-        const int h = s.cnt[par][t];
-        s.cnt[par ^ 1][t] = 0;      // counts of the next round
+        int h[BPT], hs = 0;
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) {
+            h[k] = s.cnt[par][t * BPT + k];
+            s.cnt[par ^ 1][t * BPT + k] = 0;   // counts of the next round
+            hs += h[k];
+        }
         int items = 0;
-        const int ts = block_scan(h, &items);
-        s.tstart[t] = ts;
-        s.delta[t] = s.base[t] - ts;   // pair position of tile slot i of bucket t: delta[t] + i
-        s.base[t] += h;
+        int ts = block_scan(hs, &items);
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) {
+            const int bk = t * BPT + k;
+            s.tstart[bk] = ts;
+            s.delta[bk] = s.base[bk] - ts;   // pair position of tile slot i of bucket bk: delta[bk] + i
+            s.base[bk] += h[k];
+            ts += h[k];
+        }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < SC_U; ++u) {
@@ -739,7 +798,8 @@ __global__ void __launch_bounds__(BLOCK, 4)
             c0 = C.ovf_base + v0;
         }
         if (nf == 0) continue;
-        s.base[t] = bstart + C.counts[(int64_t)t * C.units + unit];
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) s.base[t * BPT + k] = bstart[k] + C.counts[(int64_t)(t * BPT + k) * C.units + unit];
         const int nr = (nf + SC_CHUNKS - 1) / SC_CHUNKS;
         if (t == 0)
             for (int k = 0; k < SC_BUF && k < nr; ++k) issue(c0, nf, k, k);
@@ -832,6 +892,208 @@ __global__ void __launch_bounds__(BLOCK)
             }
         }
     }
+}
+
+// rank[element] from the pairs through shared-memory windows. A cluster of
+// PW_CS blocks places one coarse bucket (2^shift consecutive ids) at a time:
+//   split   block i takes slice i of the bucket's pairs in tiles of PW_TILE,
+//           stages each tile in shared memory and writes it to its scratch row
+//           grouped by window (the bucket's ids cut into PW_CS windows of
+//           2^fw_log), with the start of every group in a tile header;
+//   sync    cluster barrier: every slice is in the scratch (in L2);
+//   fill    block d reads window d's group of every tile of every slice and
+//           stores each rank into its shared-memory copy of the window;
+//   write   block d writes the window to rank with coalesced 16-byte stores.
+// Every rank write is a shared-memory store, and rank is written once, in
+// order, instead of by random 4-byte stores into L2. The scratch holds two
+// buckets per cluster (double buffered: a block splits bucket k + 1 while
+// another still fills from bucket k; both finish before bucket k + 2 reuses
+// it, since every block passes the barrier of bucket k + 1 after its fill of
+// bucket k). All blocks of a cluster take the same buckets, so they meet the
+// same barriers.
+constexpr int PW_CS = 8;                    // blocks per cluster = windows per bucket
+constexpr int PW_THREADS = 1024;
+constexpr int PW_TILE = 4096;               // pairs per staged tile (32 KB)
+constexpr int PW_FW_LOG_MAX = 15;           // windows of up to 2^15 ranks (128 KB)
+constexpr int PW_FW_LOG_MIN = 6;
+constexpr int PW_MAX_CLUSTERS = 20;         // scratch is sized for this many clusters
+
+struct PlaceWin {
+    const uint64_t* pairs;
+    const int* totals;     // [nb] pairs per bucket
+    int nb;                // buckets (at most NBK_MAX)
+    int nb_used;           // buckets that hold ids: ceil(n / 2^shift)
+    int shift;             // bucket of id x: x >> shift
+    int fw_log;            // window: 2^fw_log ids = 2^shift / PW_CS
+    int ntile;             // tiles per scratch row: ceil(2^fw_log / PW_TILE)
+    int64_t n;
+    uint64_t* scratch;     // [clusters][2][PW_CS][2^fw_log] pairs
+    int* hdr;              // [clusters][2][PW_CS][ntile][PW_CS + 1] group starts
+};
+constexpr size_t pw_smem(int fw_log) { return (sizeof(int32_t) << fw_log) + sizeof(uint64_t) * PW_TILE; }
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(PW_CS, 1, 1) __launch_bounds__(PW_THREADS, 1)
+    rs_place_win(PlaceWin P, int32_t* __restrict__ rank, DevCtl* ctl) {
+    extern __shared__ __align__(16) unsigned char pw_raw[];
+    int32_t* win = reinterpret_cast<int32_t*>(pw_raw);
+    uint64_t* tile = reinterpret_cast<uint64_t*>(pw_raw + (sizeof(int32_t) << P.fw_log));
+    __shared__ int s_start[NBK_MAX];          // start of every bucket in the pair array
+    __shared__ int s_cnt[PW_CS], s_cur[PW_CS];
+    __shared__ int s_warp[PW_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int me = (int)(blockIdx.x % PW_CS);   // rank in the cluster (1-D grid, 1-D clusters)
+    const int q = (int)(blockIdx.x / PW_CS), Q = (int)(gridDim.x / PW_CS);
+    const int FW = 1 << P.fw_log;
+    const int64_t CB = int64_t(1) << P.shift;
+    const int HW = PW_CS + 1;
+    // exclusive scan of the bucket totals (nb <= NBK_MAX = PW_THREADS)
+    {
+        const int v = t < P.nb ? P.totals[t] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < wid; ++w) off += s_warp[w];
+        if (t < P.nb) s_start[t] = off + incl - v;
+        __syncthreads();
+    }
+    const uint64_t pol = policy_evict_first();
+    int k = 0;
+    for (int b = q; b < P.nb_used; b += Q, ++k) {
+        const int buf = k & 1;
+        const int64_t bbase = (int64_t)b << P.shift;
+        const int expect = (int)max((int64_t)0, min(CB, P.n - bbase));
+        int L = P.totals[b];
+        if (L != expect || (int64_t)s_start[b] + L > P.n) {
+            // only an invalid list changes a bucket's count (the walk reports it too);
+            // the slices stay inside the scratch rows and the pairs the scatter wrote
+            if (t == 0 && me == 0) record_error(ctl, LRCC_ERR_INVALID_INPUT, -7);
+            L = (int)max((int64_t)0, min(min((int64_t)L, CB), P.n - (int64_t)s_start[b]));
+        }
+        const int per = (L + PW_CS - 1) / PW_CS;
+        const int64_t slot = ((int64_t)q * 2 + buf) * PW_CS;
+        // ---- split: slice `me` of the bucket into its scratch row, grouped by window
+        {
+            const int s0 = min(L, me * per), s1 = min(L, s0 + per);
+            uint64_t* row = P.scratch + (slot + me) * (int64_t)FW;
+            int* hdr = P.hdr + (slot + me) * (int64_t)P.ntile * HW;
+            const uint64_t* src = P.pairs + s_start[b];
+            for (int t0 = s0, ti = 0; t0 < s1; t0 += PW_TILE, ++ti) {
+                const int cnt = min(PW_TILE, s1 - t0);
+                if (t < PW_CS) s_cnt[t] = 0;
+                __syncthreads();
+                // every warp runs whole iterations (cnt is the same for the block), so the
+                // warp-wide match below sees all 32 lanes; d = -1 marks no pair / a bad id
+                for (int j0 = 0; j0 < cnt; j0 += PW_THREADS) {
+                    const int j = j0 + t;
+                    int d = -1;
+                    if (j < cnt) {
+                        uint64_t p;
+                        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
+                                     : "=l"(p) : "l"(src + t0 + j), "l"(pol));
+                        tile[j] = p;
+                        const uint32_t local = lo32(p) - (uint32_t)bbase;
+                        if (local < (uint32_t)CB) d = (int)(local >> P.fw_log);
+                        else record_error(ctl, LRCC_ERR_INVALID_INPUT, -8);
+                    }
+                    const unsigned peers = __match_any_sync(0xffffffffu, d);
+                    if (d >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
+                }
+                __syncthreads();
+                if (t == 0) {
+                    int run = 0;
+                    for (int d = 0; d < PW_CS; ++d) {
+                        hdr[ti * HW + d] = run;
+                        s_cur[d] = run;
+                        run += s_cnt[d];
+                    }
+                    hdr[ti * HW + PW_CS] = run;
+                }
+                __syncthreads();
+                uint64_t* seg = row + (t0 - s0);
+                for (int j0 = 0; j0 < cnt; j0 += PW_THREADS) {
+                    const int j = j0 + t;
+                    int d = -1;
+                    uint64_t p = 0;
+                    if (j < cnt) {
+                        p = tile[j];
+                        const uint32_t local = lo32(p) - (uint32_t)bbase;
+                        if (local < (uint32_t)CB) d = (int)(local >> P.fw_log);
+                    }
+                    const unsigned peers = __match_any_sync(0xffffffffu, d);
+                    const int leader = __ffs(peers) - 1;
+                    int base = 0;
+                    if (d >= 0 && lane == leader) base = atomicAdd(&s_cur[d], __popc(peers));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (d >= 0) seg[base + __popc(peers & lanemask_lt())] = p;
+                }
+                __syncthreads();
+            }
+        }
+        __threadfence();
+        cluster_sync_all();
+        // ---- fill: window `me` of the bucket from every slice's group
+        const int64_t wbase = bbase + (int64_t)me * FW;
+        for (int i = 0; i < PW_CS; ++i) {
+            const int s0 = min(L, i * per), s1 = min(L, s0 + per);
+            const uint64_t* row = P.scratch + (slot + i) * (int64_t)FW;
+            const int* hdr = P.hdr + (slot + i) * (int64_t)P.ntile * HW;
+            for (int t0 = s0, ti = 0; t0 < s1; t0 += PW_TILE, ++ti) {
+                const int a = ld_cg(hdr + ti * HW + me), e = ld_cg(hdr + ti * HW + me + 1);
+                const uint64_t* seg = row + (t0 - s0);
+                for (int j = a + t; j < e; j += PW_THREADS) {
+                    const uint64_t p = ld_cg_u64(seg + j);
+                    const uint32_t local = lo32(p) - (uint32_t)wbase;
+                    if (local < (uint32_t)FW) win[local] = (int32_t)hi32(p);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- write: the window's ranks, in order
+        const int wn = (int)max((int64_t)0, min((int64_t)FW, P.n - wbase));
+        int32_t* out = rank + wbase;
+        if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+            const int nv = wn >> 2;
+            for (int j = t; j < nv; j += PW_THREADS)
+                __stcs(reinterpret_cast<int4*>(out) + j, reinterpret_cast<const int4*>(win)[j]);
+            for (int j = (nv << 2) + t; j < wn; j += PW_THREADS) out[j] = win[j];
+        } else {
+            for (int j = t; j < wn; j += PW_THREADS) out[j] = win[j];
+        }
+        __syncthreads();
+    }
+}
+
+// Clusters of rs_place_win that fit on the device at once (cached per device
+// and shared-memory size); at least one.
+int place_win_clusters(Ctx* c, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(c->device, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const void* k = (const void*)rs_place_win;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(PW_CS, 1, 1);
+    cfg.blockDim = dim3(PW_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess || nc < 1) {
+        cudaGetLastError();
+        nc = std::max(1, c->sms / PW_CS);
+    }
+    cache[key] = nc;
+    return nc;
 }
 
 // Expand at level >= 1: S[c] = S_next[owner] - prefix (RS5).
@@ -1557,7 +1819,7 @@ int rs_walk_grid_current(const Plan& p) {
     return per_sm * sms;
 }
 
-RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
+RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1, int64_t given1) {
     RsLayout L;
     L.size[0] = n;
     size_t off = 0;
@@ -1579,7 +1841,8 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
         if (lvl == MAX_LEVELS - 1)  // last allowed level must fit one block
             while (logD < 30 && ((cur + (int64_t(1) << logD) - 1) >> logD) > p.rs_small) ++logD;
         // level 1 may hold extra splitters (the heads of batched lists ranked as one list)
-        const int64_t nb = ((cur + (int64_t(1) << logD) - 1) >> logD) + (lvl == 0 ? extra1 : 0);
+        int64_t nb = ((cur + (int64_t(1) << logD) - 1) >> logD) + (lvl == 0 ? extra1 : 0);
+        if (lvl == 0 && given1 > 0) nb = given1;   // first-level splitters chosen by the caller
         L.logD[lvl] = logD;
         ++lvl;
         L.size[lvl] = nb;
@@ -1612,9 +1875,27 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1) {
         L.off_ids = take(sizeof(int32_t) * CIDS * (size_t)chunks);
         L.off_meta = take(sizeof(uint64_t) * (size_t)chunks);
         L.off_fill = take(sizeof(int) * (size_t)G);
-        L.off_counts = take(sizeof(int) * (size_t)NBK * (size_t)L.units);
-        L.off_totals = take(sizeof(int) * (size_t)NBK);
+        int lg = 0;
+        while ((int64_t(1) << lg) < n) ++lg;
+        L.nb_log = std::min(NBK_LOG_MAX, std::max(NBK_LOG_MIN, lg - 18));
+        L.off_counts = take(sizeof(int) * ((size_t)1 << L.nb_log) * (size_t)L.units);
+        L.off_totals = take(sizeof(int) * ((size_t)1 << L.nb_log));
         L.off_vis = take(sizeof(uint32_t) * (size_t)((n + 31) / 32));
+        // placement through shared-memory windows: a bucket of 2^shift ids is cut
+        // into PW_CS windows of 2^fw_log ranks, each within one block's shared memory
+        const int shift = std::max(0, lg - L.nb_log);
+        int cs_log = 0;
+        while ((1 << cs_log) < PW_CS) ++cs_log;
+        const int fw_log = shift - cs_log;
+        if (fw_log >= PW_FW_LOG_MIN && fw_log <= PW_FW_LOG_MAX) {
+            L.pw = true;
+            L.pw_fw_log = fw_log;
+            const int64_t used = (n + (int64_t(1) << shift) - 1) >> shift;
+            L.pw_clusters = (int)std::min<int64_t>(used, PW_MAX_CLUSTERS);
+            L.pw_ntile = ((1 << fw_log) + PW_TILE - 1) / PW_TILE;
+            L.off_pw_scratch = take(sizeof(uint64_t) * ((size_t)L.pw_clusters * 2 * PW_CS) << fw_log);
+            L.off_pw_hdr = take(sizeof(int) * (size_t)L.pw_clusters * 2 * PW_CS * L.pw_ntile * (PW_CS + 1));
+        }
     }
     L.bytes = off;
     return L;
@@ -1674,7 +1955,9 @@ size_t lr_wyllie_ws(int64_t n, const Plan&) { return 2 * align_up(sizeof(uint64_
 
 lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
                           int32_t* rank, const Plan& p, const RsLayout& L, const int32_t* val,
-                          const BatchUnion* U) {
+                          const BatchUnion* U, const int32_t* given, int64_t given_r) {
+    // caller-chosen first-level splitters need the in-place first level
+    if (given && (L.readonly || L.split || U)) return LRCC_ERR_ARG;
     // batched lists ranked as one list need the read-only first level
     if (U && (!L.readonly || val)) return LRCC_ERR_ARG;
     // weighted sums use the in-place first level (the others count positions)
@@ -1704,10 +1987,14 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         phase_begin(c, s);
         if (vec)
             rs_select0<true><<<g, BLOCK, 0, s>>>(succ, val, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1],
-                                                 seed0, ctl);
+                                                 seed0, ctl, given == nullptr);
         else
             rs_select0<false><<<g, BLOCK, 0, s>>>(succ, val, n, head, W0, SN(1), SW(1), L.logD[0], L.size[1],
-                                                  seed0, ctl);
+                                                  seed0, ctl, given == nullptr);
+        if (given) {
+            const int gm = stream_grid(c, given_r, (const void*)rs_mark_given);
+            rs_mark_given<<<gm, BLOCK, 0, s>>>(W0, n, head, given, given_r, SN(1), SW(1), ctl);
+        }
         phase_end(c, s, PH_SELECT0);
     }
     Level0 L0;
@@ -1760,7 +2047,8 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     C.ovf_base = L.grid * L.cap;
     int lg = 0;
     while ((int64_t(1) << lg) < n) ++lg;
-    C.shift = std::max(0, lg - NBK_LOG);
+    C.nb = 1 << L.nb_log;
+    C.shift = std::max(0, lg - L.nb_log);
     C.careful = int64_t(32) << L.logD[0];
     auto walk = [&](int l, uint64_t* Wl, int64_t nl) {
         const int r = (int)L.size[l + 1];
@@ -1781,7 +2069,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     if (L.readonly) {
         cudaMemsetAsync(C.vis, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
         // overflow units' counts are accumulated with atomics (own units are stored whole)
-        cudaMemsetAsync(C.counts, 0, sizeof(int) * (size_t)NBK * (size_t)L.units, s);
+        cudaMemsetAsync(C.counts, 0, sizeof(int) * (size_t)C.nb * (size_t)L.units, s);
         const int G = (int)L.grid;
         phase_begin(c, s);
         if (p.rs_chains >= 4) rs_walk0c<4><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
@@ -1789,7 +2077,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         else rs_walk0c<1><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
         phase_end(c, s, PH_WALK0);
         phase_begin(c, s);
-        rs_scan_counts<<<NBK, SCAN_THREADS, 0, s>>>(C.counts, L.units, C.totals);
+        rs_scan_counts<<<C.nb, SCAN_THREADS, 0, s>>>(C.counts, L.units, C.totals);
         phase_end(c, s, PH_SCAN);
         if (U) {
             phase_begin(c, s);
@@ -1857,13 +2145,41 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     }
     if (L.readonly) {
         phase_begin(c, s);
-        cudaFuncSetAttribute((const void*)rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM);
-        const int gs = std::min((int)L.grid, persistent_grid(c, (const void*)rs_scatter, BLOCK, SC_SMEM));
-        rs_scatter<<<gs, BLOCK, SC_SMEM, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
+        auto scatter = [&](auto nbc) {
+            constexpr int NB = decltype(nbc)::value;
+            const void* k = (const void*)rs_scatter<NB>;
+            const size_t smem = sizeof(ScatterSmem<NB>);
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const int gs = std::min((int)L.grid, persistent_grid(c, k, BLOCK, smem));
+            rs_scatter<NB><<<gs, BLOCK, smem, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
+        };
+        if (L.nb_log == 8) scatter(std::integral_constant<int, 256>());
+        else if (L.nb_log == 9) scatter(std::integral_constant<int, 512>());
+        else scatter(std::integral_constant<int, 1024>());
         phase_end(c, s, PH_SCATTER);
-        const int g = 2 * c->sms;
         phase_begin(c, s);
-        rs_place<<<g, BLOCK, 0, s>>>(W0, n, rank, ctl);
+        if (L.pw) {
+            PlaceWin P;
+            P.pairs = W0;
+            P.totals = C.totals;
+            P.nb = C.nb;
+            P.shift = C.shift;
+            P.nb_used = (int)((n + (int64_t(1) << C.shift) - 1) >> C.shift);
+            P.fw_log = L.pw_fw_log;
+            P.ntile = L.pw_ntile;
+            P.n = n;
+            P.scratch = reinterpret_cast<uint64_t*>(base + L.off_pw_scratch);
+            P.hdr = reinterpret_cast<int*>(base + L.off_pw_hdr);
+            const size_t smem = pw_smem(L.pw_fw_log);
+            // the kernel's limit is the largest window's, set before every launch
+            // (a smaller limit left by another call would make a larger launch fail)
+            cudaFuncSetAttribute((const void*)rs_place_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pw_smem(PW_FW_LOG_MAX));
+            const int clusters = std::min(L.pw_clusters, place_win_clusters(c, smem));
+            rs_place_win<<<clusters * PW_CS, PW_THREADS, smem, s>>>(P, rank, ctl);
+        } else {
+            rs_place<<<2 * c->sms, BLOCK, 0, s>>>(W0, n, rank, ctl);
+        }
         phase_end(c, s, PH_EXPAND0);
     } else if (L.split) {
         phase_begin(c, s);

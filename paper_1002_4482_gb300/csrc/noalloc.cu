@@ -9,13 +9,19 @@
 // the first call on each stream; this variant never does.
 //
 // How: its scratch (the 8-byte walk words, the deeper ruling-set levels and
-// the control block) is one file-scope __device__ array of fixed size that
-// every GPU loading the library holds until the process exits. Host code
-// cannot use the array's name as a device address, so the first call on each
-// device looks the address up with cudaGetSymbolAddress while that device is
-// current, and passes it to the kernels. That first call should be made
-// before any stream capture. The call makes no cudaMalloc, cudaFree,
-// cudaStreamCreate or cudaEventCreate call.
+// the control block) is one file-scope __device__ array of fixed size that a
+// GPU holds, once it has it, until the process exits. Host code cannot use the
+// array's name as a device address, so the first call on each device looks
+// the address up with cudaGetSymbolAddress while that device is current, and
+// passes it to the kernels. With CUDA's default lazy module loading the
+// library's device code, this array included, is loaded onto a device at that
+// first lookup: the array's memory is committed during the first call on
+// each device, not when the library is loaded, and that first call can fail
+// for lack of memory (LRCC_ERR_CUDA). A caller with a fixed budget makes one
+// warm-up call per device while setting up (or runs with
+// CUDA_MODULE_LOADING=EAGER, which loads the module when the context is
+// created). That first call should also come before any stream capture. The
+// call makes no cudaMalloc, cudaFree, cudaStreamCreate or cudaEventCreate call.
 //
 // Limits: at most NOALLOC_MAX_N elements. All calls on a device share the one
 // array and it keeps the last call's contents: the control counters are

@@ -386,6 +386,36 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
     return lr_rank_locked(c, succ, n, head, rank);
 }
 
+lrcc_status lr_rank_splitters(const int32_t* succ, int64_t n, int32_t head, const int32_t* spl, int64_t r,
+                              int32_t* rank, void* stream) {
+    if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
+    if (n == 0) return LRCC_OK;
+    if (!succ || !rank || !spl || head < 0 || head >= n || r < 1 || r > n) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Plan p = plan_for(KIND_LR, n);
+    p.rs_level0 = 1;   // the in-place first level carries the given splitters in its words
+    const RsLayout L = rs_layout(n, p, rs_walk_grid(c, p), 0, r);
+    if (n > p.rs_small) {
+        st = ensure_ws(c, L.bytes);
+        if (st != LRCC_OK) return st;
+    }
+    std::vector<uint64_t> key = {8, (uint64_t)succ, (uint64_t)n, (uint64_t)head, (uint64_t)rank, (uint64_t)spl,
+                                 (uint64_t)r};
+    const auto pk = plan_key(p);
+    key.insert(key.end(), pk.begin(), pk.end());
+    st = launch_recorded(c, p, key, [&](cudaStream_t s) {
+        reset_ctl(c, s);
+        return lr_enqueue_rs(c, s, succ, n, head, rank, p, L, nullptr, nullptr, spl, r);
+    });
+    c->last_kind = KIND_LR;
+    c->last_levels = n > p.rs_small ? L.levels : 0;
+    for (int l = 0; l < MAX_LEVELS; ++l) c->last_splitter_cap[l] = l < L.levels ? L.size[l + 1] : 0;
+    return st;
+}
+
 lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t head, int32_t* out, void* stream) {
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
@@ -575,6 +605,16 @@ lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64
         return LRCC_ERR_CUDA;
     if (total < 0) return LRCC_ERR_ARG;
     return cc_label_batched_sized(src, dst, edge_off, vert_off, num_graphs, total, label, stream);
+}
+
+lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m, const int32_t* table, int64_t n,
+                              int64_t* out, void* stream) {
+    if (m < 0 || n < 1 || !out || !table || (m > 0 && (!src || !dst))) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return cc_gather_probe_run(c, src, dst, m, table, n, out);
 }
 
 lrcc_status lrcc_wait_check(int polls, void* stream) {

@@ -189,6 +189,42 @@ def test_overflow_pool_carries_long_sublists():
         _restore_level0()
 
 
+@pytest.mark.parametrize("n", [(1 << 16) + 1, (1 << 17) + 5, 3 * (1 << 20) + 7, (1 << 24) - 3])
+def test_read_only_level_window_placement(n):
+    # the read-only first level places ranks through shared-memory windows once a
+    # bucket's window holds at least 64 ranks: windows of 2^6 .. 2^13 here, with
+    # a partial last bucket and windows wholly past n; closed form of the layout
+    base = lrcc.get_plan(lrcc.KIND_LR, n)
+    try:
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=2)
+        for seed in (3, 4):
+            succ, head, perm = gen.list_random(n, seed, with_perm=True)
+            r = _run("rs", succ, head)
+            assert np.array_equal(r[perm], np.arange(n - 1, -1, -1, dtype=np.int32)), seed
+        succ, head = gen.list_ordered(n)
+        assert np.array_equal(_run("rs", succ, head), np.arange(n - 1, -1, -1, dtype=np.int32))
+    finally:
+        lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=base["rs_level0"])
+        _restore_level0()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [(1 << 26) + 12345, (1 << 27) + 777])
+def test_read_only_level_512_and_1024_buckets(n):
+    # lists of 2^26 .. 2^27 elements take 512 coarse buckets, up to 2^28 take 1024
+    # (2^18 ids each, cut into eight windows of 2^15 ranks); random and ordered layouts
+    succ, head, perm = gen.list_random(n, 5, with_perm=True)
+    t = torch.from_numpy(succ).to(DEV)
+    rank = lrcc.lr_rank(t, head)
+    lrcc.check()
+    assert np.array_equal(rank.cpu().numpy()[perm], np.arange(n - 1, -1, -1, dtype=np.int32))
+    del t, rank
+    succ, head = gen.list_ordered(n)
+    rank = lrcc.lr_rank(torch.from_numpy(succ).to(DEV), head)
+    lrcc.check()
+    assert np.array_equal(rank.cpu().numpy(), np.arange(n - 1, -1, -1, dtype=np.int32))
+
+
 @pytest.mark.slow
 def test_full_size_2p28_random_and_ordered():
     # the bench workload: n = 2^28 in random layout; checked exactly against the
@@ -239,3 +275,32 @@ def test_bounded_wait_records_timeout():
         lrcc.wait_check(0)
     succ, head = gen.list_random(100_003, 5)
     assert np.array_equal(_run("rs", succ, head), oracle.lr_rank(succ, head))
+
+
+@pytest.mark.parametrize("n", [20_001, 1 << 20, 3_000_017])
+def test_given_splitters_even_and_random(n):
+    # ranks are the same with the paper's perfect even splitters (list positions
+    # 0, D, 2D, ...: sublists of exactly D elements) and with random ones
+    succ, head, perm = gen.list_random(n, 41, with_perm=True)
+    t = torch.from_numpy(succ).to(DEV)
+    expect = np.arange(n - 1, -1, -1, dtype=np.int32)
+    for D in (8, 32, 1000):
+        even = torch.from_numpy(np.ascontiguousarray(perm[::D])).to(DEV)
+        r = lrcc.lr_rank_splitters(t, head, even)
+        lrcc.check()
+        assert np.array_equal(r.cpu().numpy()[perm], expect), D
+        rnd = np.random.default_rng(D).choice(np.arange(1, n), size=(n + D - 1) // D - 1, replace=False)
+        spl = np.concatenate([[head], perm[np.sort(rnd)]]).astype(np.int32)
+        r = lrcc.lr_rank_splitters(t, head, torch.from_numpy(spl).to(DEV))
+        lrcc.check()
+        assert np.array_equal(r.cpu().numpy()[perm], expect), D
+
+
+def test_given_splitters_errors():
+    succ, head, perm = gen.list_random(50_000, 42, with_perm=True)
+    t = torch.from_numpy(succ).to(DEV)
+    for bad in (perm[1::16], np.concatenate([perm[::16], perm[16:17]]), np.concatenate([perm[::16], [60_000]])):
+        lrcc.lr_rank_splitters(t, head, torch.from_numpy(np.ascontiguousarray(bad, np.int32)).to(DEV))
+        assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
+    with pytest.raises(lrcc.LrccError):
+        lrcc.lr_rank_splitters(t, head, torch.zeros(0, dtype=torch.int32, device=DEV))

@@ -82,7 +82,8 @@ def run_case(argv):
 
         lr 26 [inplace|readonly|split]   lr_rank, random list of 2^26
         wyllie 24                        lr_rank_wyllie
-        cc 22                            cc_label, R-MAT scale 22, edge factor 16
+        cc 22                            cc_label, R-MAT scale 22, edge factor 16, then the
+                                         gather probe over the same edges
         batch 10                         2^10 mixed instances, both batched calls
     """
     import torch
@@ -107,9 +108,13 @@ def run_case(argv):
         assert np.array_equal(r[perm], np.arange((1 << log2) - 1, -1, -1, dtype=np.int32))
     elif what == "cc":
         src, dst, n = workloads.cc_rmat(log2, 16)
-        lab = lrcc.cc_label(torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev), n)
+        sd, dd = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
+        lab_d = lrcc.cc_label(sd, dd, n)
         lrcc.check()
-        lab = lab.cpu().numpy()
+        # the hook pass's traffic without the hooking, over the same edges (its ceiling)
+        lrcc.gather_probe(sd, dd, lab_d)
+        lrcc.check()
+        lab = lab_d.cpu().numpy()
         assert np.array_equal(lab[src], lab[dst]) and (lab <= np.arange(n)).all()
         assert np.array_equal(lab[lab], lab)
         log("rounds", lrcc.last_stats()["rounds"])
@@ -825,6 +830,22 @@ def main():
     lrcc.check(stream)
     probe_ms = p0.elapsed_time(p1) / 3
 
+    # the first pass over all edges alone: one call with plain launches (the host
+    # drives the loop, so each pass is its own launch) and phase timing on
+    cc_graphs = lrcc.get_plan(lrcc.KIND_CC, n_cc)["use_graphs"]
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=2)
+    lrcc.set_timing(True)
+    lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
+    lrcc.phase_times(stream)
+    full_pass = []
+    for _ in range(3):
+        lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
+        full_pass.append(lrcc.phase_times(stream).get("cc_hook_full", (float("nan"), 0))[0])
+    lrcc.set_timing(False)
+    lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=cc_graphs)
+    lrcc.check(stream)
+    full_pass_ms = min(full_pass)
+
     lr_ms = sum(v[0] for k, v in phases.items() if k.startswith(("rs_", "lr_small"))) / args.steps
     cc_ms = sum(v[0] for k, v in phases.items() if k.startswith("cc_")) / args.steps
     launches_lr = sum(v[1] for k, v in phases.items() if k.startswith(("rs_", "lr_small")))
@@ -1075,9 +1096,12 @@ def main():
                            "edges_read": cc_stats["edges_read"],
                            "ceiling_ms": cc_stats["edges_read"] / (m_cc / probe_ms),
                            "frac": (cc_stats["edges_read"] / (m_cc / probe_ms)) / cc_ms if cc_ms else None,
+                           "full_pass_ms": full_pass_ms, "full_pass_frac": probe_ms / full_pass_ms,
                            "note": "probe: the hook pass's 16-byte edge stream and two gathers per edge (L1, "
                                    "evict-last) over a 4n-byte table, no hooking (lrcc_gather_probe); ceiling: "
-                                   "every edge the hook passes read, at the probe's rate; frac = ceiling / cc ms"}},
+                                   "every edge the hook passes read, at the probe's rate; frac = ceiling / cc ms; full_pass: the "
+                                   "loop's first pass over all edges alone (plain launches, best of 3), full_pass_frac "
+                                   "= probe / full pass"}},
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
                 "batched": batched, "serving": serving, "cc_families": families, "lr_sweep": sweep,
                 "even_vs_random_splitters": even, "small_configs": small,

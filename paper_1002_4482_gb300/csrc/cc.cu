@@ -344,8 +344,8 @@ struct CcArgs {
 };
 
 // Enqueues one round's hook pass, and (separately) its shortcut pass; the
-// loop control runs between them.
-lrcc_status enqueue_hook(Ctx* c, cudaStream_t s, const CcArgs& a) {
+// loop control runs between them. `phase` names the pass in timing mode.
+lrcc_status enqueue_hook(Ctx* c, cudaStream_t s, const CcArgs& a, int phase = PH_CC_HOOK) {
     const bool ve = aligned16(a.src) && aligned16(a.dst);
     const bool vn = aligned16(a.label);
     const void* hk = ve ? (const void*)cc_hook<true> : (const void*)cc_hook<false>;
@@ -356,7 +356,7 @@ lrcc_status enqueue_hook(Ctx* c, cudaStream_t s, const CcArgs& a) {
         phase_begin(c, s);
         if (ve) cc_hook<true><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, a.act, c->ctl);
         else cc_hook<false><<<g, BLOCK, 0, s>>>(a.src, a.dst, a.m, a.label, a.n, a.mode, a.act, c->ctl);
-        phase_end(c, s, PH_CC_HOOK);
+        phase_end(c, s, phase);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -516,7 +516,8 @@ lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, in
     if (cudaMallocHost(&host_flag, sizeof(int)) != cudaSuccess) return LRCC_ERR_NOMEM;
     lrcc_status st = LRCC_OK;
     for (int r = 0; r < a.cap + 1; ++r) {
-        st = enqueue_hook(c, s, a);
+        // the first pass of the loop reads every edge (later ones the active edges)
+        st = enqueue_hook(c, s, a, r == 0 ? PH_CC_HOOK_FULL : PH_CC_HOOK);
         if (st != LRCC_OK) break;
         cc_control_host<<<1, 1, 0, s>>>(c->ctl, a.cap, a.act.cap > 0);
         st = enqueue_shortcut(c, s, a);

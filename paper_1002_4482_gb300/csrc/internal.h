@@ -54,10 +54,6 @@ struct RsLayout {
     int nb_log = 8;                 // coarse id buckets of the scatter: 2^nb_log
     size_t off_ids = 0, off_meta = 0, off_fill = 0, off_counts = 0, off_totals = 0,
         off_vis = 0;
-    // placement through shared-memory windows (read-only level 0)
-    bool pw = false;
-    int pw_fw_log = 0, pw_clusters = 0, pw_ntile = 0;
-    size_t off_pw_scratch = 0, off_pw_hdr = 0;
     size_t bytes = 0;
 };
 // extra1: extra first-level splitters (the heads of batched lists ranked as one list)
@@ -86,7 +82,7 @@ int rs_walk_grid_current(const Plan& p);
 enum Phase {
     PH_SELECT0, PH_WALK0, PH_SELECT, PH_WALK, PH_FINAL, PH_EXPAND, PH_EXPAND0, PH_SMALL,
     PH_WY_PACK, PH_WY_JUMP, PH_WY_FINAL, PH_CC_INIT, PH_CC_LOOP, PH_CC_HOOK, PH_CC_SHORTCUT,
-    PH_LR_BATCH, PH_CC_BATCH, PH_BATCH_PREP, PH_SCAN, PH_SCATTER, PH_COUNT
+    PH_LR_BATCH, PH_CC_BATCH, PH_BATCH_PREP, PH_SCAN, PH_SCATTER, PH_CC_HOOK_FULL, PH_COUNT
 };
 
 struct GraphEntry {

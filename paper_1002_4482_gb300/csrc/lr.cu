@@ -16,8 +16,6 @@
 // the tail, itself included); the final rank is S - 1.
 #include <algorithm>
 #include <cmath>
-#include <map>
-#include <mutex>
 #include <type_traits>
 
 #include "block_wyllie.cuh"
@@ -348,12 +346,11 @@ __global__ void __launch_bounds__(BLOCK)
 // splitter cannot trap it; valid lists never repeat an element.
 
 constexpr int CIDS = 8;        // element ids per chunk (one 32-byte sector)
-// Coarse id buckets: 2^8 up to lists of 2^26 elements, then 2^(lg - 18) so that
-// one bucket holds at most 2^18 ids (the reach of one placement cluster), at
-// most 2^10.
-constexpr int NBK_LOG_MIN = 8;
-constexpr int NBK_LOG_MAX = 10;
-constexpr int NBK_MAX = 1 << NBK_LOG_MAX;
+// Coarse id buckets of the scatter (a bucket's rank writes stay in L2 while
+// rs_place works through it). More buckets make each round's runs shorter:
+// with 1024 buckets at 2^28 elements the scatter took 2.67 ms instead of 1.41.
+constexpr int NBK_LOG = 8;
+constexpr int NBK = 1 << NBK_LOG;
 constexpr int NSEG = 4;        // scatter work units per walk block region
 
 struct Level0 {
@@ -382,7 +379,7 @@ struct Chunks {
     int64_t ovf_cap;     // overflow chunks
     int64_t ovf_base;    // index of the first overflow chunk (= grid * cap)
     int shift;           // coarse bucket of element x = x >> shift
-    int nb;              // coarse buckets (2^NBK_LOG_MIN .. NBK_MAX)
+    int nb;              // coarse buckets (NBK)
     int64_t careful;     // steps after which a walk marks what it visits
 };
 
@@ -421,7 +418,7 @@ __global__ void __launch_bounds__(BLOCK)
     }
     constexpr int WCHUNK = 64;
     __shared__ int s_fill;
-    __shared__ int s_cnt[NSEG * NBK_MAX];   // [segment][bucket], nb buckets per segment
+    __shared__ int s_cnt[NSEG * NBK];   // [segment][bucket], nb buckets per segment
     for (int t = threadIdx.x; t < NSEG * C.nb; t += BLOCK) s_cnt[t] = 0;
     if (threadIdx.x == 0) s_fill = 0;
     __syncthreads();
@@ -858,6 +855,9 @@ namespace {
 // line is complete (a grid-stride loop would let blocks drift apart and
 // spread the writes over far more memory than L2 holds).
 constexpr int PLACE_SLICE = BLOCK * 64;
+#ifndef LRCC_PLACE_BLOCKS_PER_SM
+#define LRCC_PLACE_BLOCKS_PER_SM 2
+#endif
 __global__ void __launch_bounds__(BLOCK)
     rs_place(const uint64_t* __restrict__ pairs, int64_t n, int32_t* __restrict__ rank, DevCtl* ctl) {
     __shared__ int s_start;
@@ -892,208 +892,6 @@ __global__ void __launch_bounds__(BLOCK)
             }
         }
     }
-}
-
-// rank[element] from the pairs through shared-memory windows. A cluster of
-// PW_CS blocks places one coarse bucket (2^shift consecutive ids) at a time:
-//   split   block i takes slice i of the bucket's pairs in tiles of PW_TILE,
-//           stages each tile in shared memory and writes it to its scratch row
-//           grouped by window (the bucket's ids cut into PW_CS windows of
-//           2^fw_log), with the start of every group in a tile header;
-//   sync    cluster barrier: every slice is in the scratch (in L2);
-//   fill    block d reads window d's group of every tile of every slice and
-//           stores each rank into its shared-memory copy of the window;
-//   write   block d writes the window to rank with coalesced 16-byte stores.
-// Every rank write is a shared-memory store, and rank is written once, in
-// order, instead of by random 4-byte stores into L2. The scratch holds two
-// buckets per cluster (double buffered: a block splits bucket k + 1 while
-// another still fills from bucket k; both finish before bucket k + 2 reuses
-// it, since every block passes the barrier of bucket k + 1 after its fill of
-// bucket k). All blocks of a cluster take the same buckets, so they meet the
-// same barriers.
-constexpr int PW_CS = 8;                    // blocks per cluster = windows per bucket
-constexpr int PW_THREADS = 1024;
-constexpr int PW_TILE = 4096;               // pairs per staged tile (32 KB)
-constexpr int PW_FW_LOG_MAX = 15;           // windows of up to 2^15 ranks (128 KB)
-constexpr int PW_FW_LOG_MIN = 6;
-constexpr int PW_MAX_CLUSTERS = 20;         // scratch is sized for this many clusters
-
-struct PlaceWin {
-    const uint64_t* pairs;
-    const int* totals;     // [nb] pairs per bucket
-    int nb;                // buckets (at most NBK_MAX)
-    int nb_used;           // buckets that hold ids: ceil(n / 2^shift)
-    int shift;             // bucket of id x: x >> shift
-    int fw_log;            // window: 2^fw_log ids = 2^shift / PW_CS
-    int ntile;             // tiles per scratch row: ceil(2^fw_log / PW_TILE)
-    int64_t n;
-    uint64_t* scratch;     // [clusters][2][PW_CS][2^fw_log] pairs
-    int* hdr;              // [clusters][2][PW_CS][ntile][PW_CS + 1] group starts
-};
-constexpr size_t pw_smem(int fw_log) { return (sizeof(int32_t) << fw_log) + sizeof(uint64_t) * PW_TILE; }
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__global__ void __cluster_dims__(PW_CS, 1, 1) __launch_bounds__(PW_THREADS, 1)
-    rs_place_win(PlaceWin P, int32_t* __restrict__ rank, DevCtl* ctl) {
-    extern __shared__ __align__(16) unsigned char pw_raw[];
-    int32_t* win = reinterpret_cast<int32_t*>(pw_raw);
-    uint64_t* tile = reinterpret_cast<uint64_t*>(pw_raw + (sizeof(int32_t) << P.fw_log));
-    __shared__ int s_start[NBK_MAX];          // start of every bucket in the pair array
-    __shared__ int s_cnt[PW_CS], s_cur[PW_CS];
-    __shared__ int s_warp[PW_THREADS / 32];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int me = (int)(blockIdx.x % PW_CS);   // rank in the cluster (1-D grid, 1-D clusters)
-    const int q = (int)(blockIdx.x / PW_CS), Q = (int)(gridDim.x / PW_CS);
-    const int FW = 1 << P.fw_log;
-    const int64_t CB = int64_t(1) << P.shift;
-    const int HW = PW_CS + 1;
-    // exclusive scan of the bucket totals (nb <= NBK_MAX = PW_THREADS)
-    {
-        const int v = t < P.nb ? P.totals[t] : 0;
-        int incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += x;
-        }
-        if (lane == 31) s_warp[wid] = incl;
-        __syncthreads();
-        int off = 0;
-        for (int w = 0; w < wid; ++w) off += s_warp[w];
-        if (t < P.nb) s_start[t] = off + incl - v;
-        __syncthreads();
-    }
-    const uint64_t pol = policy_evict_first();
-    int k = 0;
-    for (int b = q; b < P.nb_used; b += Q, ++k) {
-        const int buf = k & 1;
-        const int64_t bbase = (int64_t)b << P.shift;
-        const int expect = (int)max((int64_t)0, min(CB, P.n - bbase));
-        int L = P.totals[b];
-        if (L != expect || (int64_t)s_start[b] + L > P.n) {
-            // only an invalid list changes a bucket's count (the walk reports it too);
-            // the slices stay inside the scratch rows and the pairs the scatter wrote
-            if (t == 0 && me == 0) record_error(ctl, LRCC_ERR_INVALID_INPUT, -7);
-            L = (int)max((int64_t)0, min(min((int64_t)L, CB), P.n - (int64_t)s_start[b]));
-        }
-        const int per = (L + PW_CS - 1) / PW_CS;
-        const int64_t slot = ((int64_t)q * 2 + buf) * PW_CS;
-        // ---- split: slice `me` of the bucket into its scratch row, grouped by window
-        {
-            const int s0 = min(L, me * per), s1 = min(L, s0 + per);
-            uint64_t* row = P.scratch + (slot + me) * (int64_t)FW;
-            int* hdr = P.hdr + (slot + me) * (int64_t)P.ntile * HW;
-            const uint64_t* src = P.pairs + s_start[b];
-            for (int t0 = s0, ti = 0; t0 < s1; t0 += PW_TILE, ++ti) {
-                const int cnt = min(PW_TILE, s1 - t0);
-                if (t < PW_CS) s_cnt[t] = 0;
-                __syncthreads();
-                // every warp runs whole iterations (cnt is the same for the block), so the
-                // warp-wide match below sees all 32 lanes; d = -1 marks no pair / a bad id
-                for (int j0 = 0; j0 < cnt; j0 += PW_THREADS) {
-                    const int j = j0 + t;
-                    int d = -1;
-                    if (j < cnt) {
-                        uint64_t p;
-                        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
-                                     : "=l"(p) : "l"(src + t0 + j), "l"(pol));
-                        tile[j] = p;
-                        const uint32_t local = lo32(p) - (uint32_t)bbase;
-                        if (local < (uint32_t)CB) d = (int)(local >> P.fw_log);
-                        else record_error(ctl, LRCC_ERR_INVALID_INPUT, -8);
-                    }
-                    const unsigned peers = __match_any_sync(0xffffffffu, d);
-                    if (d >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[d], __popc(peers));
-                }
-                __syncthreads();
-                if (t == 0) {
-                    int run = 0;
-                    for (int d = 0; d < PW_CS; ++d) {
-                        hdr[ti * HW + d] = run;
-                        s_cur[d] = run;
-                        run += s_cnt[d];
-                    }
-                    hdr[ti * HW + PW_CS] = run;
-                }
-                __syncthreads();
-                uint64_t* seg = row + (t0 - s0);
-                for (int j0 = 0; j0 < cnt; j0 += PW_THREADS) {
-                    const int j = j0 + t;
-                    int d = -1;
-                    uint64_t p = 0;
-                    if (j < cnt) {
-                        p = tile[j];
-                        const uint32_t local = lo32(p) - (uint32_t)bbase;
-                        if (local < (uint32_t)CB) d = (int)(local >> P.fw_log);
-                    }
-                    const unsigned peers = __match_any_sync(0xffffffffu, d);
-                    const int leader = __ffs(peers) - 1;
-                    int base = 0;
-                    if (d >= 0 && lane == leader) base = atomicAdd(&s_cur[d], __popc(peers));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (d >= 0) seg[base + __popc(peers & lanemask_lt())] = p;
-                }
-                __syncthreads();
-            }
-        }
-        __threadfence();
-        cluster_sync_all();
-        // ---- fill: window `me` of the bucket from every slice's group
-        const int64_t wbase = bbase + (int64_t)me * FW;
-        for (int i = 0; i < PW_CS; ++i) {
-            const int s0 = min(L, i * per), s1 = min(L, s0 + per);
-            const uint64_t* row = P.scratch + (slot + i) * (int64_t)FW;
-            const int* hdr = P.hdr + (slot + i) * (int64_t)P.ntile * HW;
-            for (int t0 = s0, ti = 0; t0 < s1; t0 += PW_TILE, ++ti) {
-                const int a = ld_cg(hdr + ti * HW + me), e = ld_cg(hdr + ti * HW + me + 1);
-                const uint64_t* seg = row + (t0 - s0);
-                for (int j = a + t; j < e; j += PW_THREADS) {
-                    const uint64_t p = ld_cg_u64(seg + j);
-                    const uint32_t local = lo32(p) - (uint32_t)wbase;
-                    if (local < (uint32_t)FW) win[local] = (int32_t)hi32(p);
-                }
-            }
-        }
-        __syncthreads();
-        // ---- write: the window's ranks, in order
-        const int wn = (int)max((int64_t)0, min((int64_t)FW, P.n - wbase));
-        int32_t* out = rank + wbase;
-        if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-            const int nv = wn >> 2;
-            for (int j = t; j < nv; j += PW_THREADS)
-                __stcs(reinterpret_cast<int4*>(out) + j, reinterpret_cast<const int4*>(win)[j]);
-            for (int j = (nv << 2) + t; j < wn; j += PW_THREADS) out[j] = win[j];
-        } else {
-            for (int j = t; j < wn; j += PW_THREADS) out[j] = win[j];
-        }
-        __syncthreads();
-    }
-}
-
-// Clusters of rs_place_win that fit on the device at once (cached per device
-// and shared-memory size); at least one.
-int place_win_clusters(Ctx* c, size_t smem) {
-    static std::mutex mu;
-    static std::map<std::pair<int, size_t>, int> cache;
-    std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(c->device, smem);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    const void* k = (const void*)rs_place_win;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(PW_CS, 1, 1);
-    cfg.blockDim = dim3(PW_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess || nc < 1) {
-        cudaGetLastError();
-        nc = std::max(1, c->sms / PW_CS);
-    }
-    cache[key] = nc;
-    return nc;
 }
 
 // Expand at level >= 1: S[c] = S_next[owner] - prefix (RS5).
@@ -1875,27 +1673,10 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1, int6
         L.off_ids = take(sizeof(int32_t) * CIDS * (size_t)chunks);
         L.off_meta = take(sizeof(uint64_t) * (size_t)chunks);
         L.off_fill = take(sizeof(int) * (size_t)G);
-        int lg = 0;
-        while ((int64_t(1) << lg) < n) ++lg;
-        L.nb_log = std::min(NBK_LOG_MAX, std::max(NBK_LOG_MIN, lg - 18));
-        L.off_counts = take(sizeof(int) * ((size_t)1 << L.nb_log) * (size_t)L.units);
-        L.off_totals = take(sizeof(int) * ((size_t)1 << L.nb_log));
+        L.nb_log = NBK_LOG;
+        L.off_counts = take(sizeof(int) * (size_t)NBK * (size_t)L.units);
+        L.off_totals = take(sizeof(int) * (size_t)NBK);
         L.off_vis = take(sizeof(uint32_t) * (size_t)((n + 31) / 32));
-        // placement through shared-memory windows: a bucket of 2^shift ids is cut
-        // into PW_CS windows of 2^fw_log ranks, each within one block's shared memory
-        const int shift = std::max(0, lg - L.nb_log);
-        int cs_log = 0;
-        while ((1 << cs_log) < PW_CS) ++cs_log;
-        const int fw_log = shift - cs_log;
-        if (fw_log >= PW_FW_LOG_MIN && fw_log <= PW_FW_LOG_MAX) {
-            L.pw = true;
-            L.pw_fw_log = fw_log;
-            const int64_t used = (n + (int64_t(1) << shift) - 1) >> shift;
-            L.pw_clusters = (int)std::min<int64_t>(used, PW_MAX_CLUSTERS);
-            L.pw_ntile = ((1 << fw_log) + PW_TILE - 1) / PW_TILE;
-            L.off_pw_scratch = take(sizeof(uint64_t) * ((size_t)L.pw_clusters * 2 * PW_CS) << fw_log);
-            L.off_pw_hdr = take(sizeof(int) * (size_t)L.pw_clusters * 2 * PW_CS * L.pw_ntile * (PW_CS + 1));
-        }
     }
     L.bytes = off;
     return L;
@@ -2145,41 +1926,14 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     }
     if (L.readonly) {
         phase_begin(c, s);
-        auto scatter = [&](auto nbc) {
-            constexpr int NB = decltype(nbc)::value;
-            const void* k = (const void*)rs_scatter<NB>;
-            const size_t smem = sizeof(ScatterSmem<NB>);
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int gs = std::min((int)L.grid, persistent_grid(c, k, BLOCK, smem));
-            rs_scatter<NB><<<gs, BLOCK, smem, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
-        };
-        if (L.nb_log == 8) scatter(std::integral_constant<int, 256>());
-        else if (L.nb_log == 9) scatter(std::integral_constant<int, 512>());
-        else scatter(std::integral_constant<int, 1024>());
+        const void* sk = (const void*)rs_scatter<NBK>;
+        const size_t smem = sizeof(ScatterSmem<NBK>);
+        cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int gs = std::min((int)L.grid, persistent_grid(c, sk, BLOCK, smem));
+        rs_scatter<NBK><<<gs, BLOCK, smem, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
         phase_end(c, s, PH_SCATTER);
         phase_begin(c, s);
-        if (L.pw) {
-            PlaceWin P;
-            P.pairs = W0;
-            P.totals = C.totals;
-            P.nb = C.nb;
-            P.shift = C.shift;
-            P.nb_used = (int)((n + (int64_t(1) << C.shift) - 1) >> C.shift);
-            P.fw_log = L.pw_fw_log;
-            P.ntile = L.pw_ntile;
-            P.n = n;
-            P.scratch = reinterpret_cast<uint64_t*>(base + L.off_pw_scratch);
-            P.hdr = reinterpret_cast<int*>(base + L.off_pw_hdr);
-            const size_t smem = pw_smem(L.pw_fw_log);
-            // the kernel's limit is the largest window's, set before every launch
-            // (a smaller limit left by another call would make a larger launch fail)
-            cudaFuncSetAttribute((const void*)rs_place_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)pw_smem(PW_FW_LOG_MAX));
-            const int clusters = std::min(L.pw_clusters, place_win_clusters(c, smem));
-            rs_place_win<<<clusters * PW_CS, PW_THREADS, smem, s>>>(P, rank, ctl);
-        } else {
-            rs_place<<<2 * c->sms, BLOCK, 0, s>>>(W0, n, rank, ctl);
-        }
+        rs_place<<<LRCC_PLACE_BLOCKS_PER_SM * c->sms, BLOCK, 0, s>>>(W0, n, rank, ctl);
         phase_end(c, s, PH_EXPAND0);
     } else if (L.split) {
         phase_begin(c, s);

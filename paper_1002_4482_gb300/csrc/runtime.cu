@@ -22,7 +22,7 @@ std::atomic<int> g_timing{0};
 const char* const kPhaseNames[PH_COUNT] = {
     "rs_select0", "rs_walk0", "rs_select", "rs_walk", "rs_final", "rs_expand", "rs_expand0", "lr_small",
     "wy_pack", "wy_jump", "wy_final", "cc_init", "cc_loop", "cc_hook", "cc_shortcut",
-    "lr_batch", "cc_batch", "batch_prep", "rs_scan", "rs_scatter"};
+    "lr_batch", "cc_batch", "batch_prep", "rs_scan", "rs_scatter", "cc_hook_full"};
 std::map<std::pair<int, cudaStream_t>, Ctx*> g_ctx;
 // per device: the streams that carry the host-buffer calls' uploads and downloads
 std::map<int, std::pair<cudaStream_t, cudaStream_t>> g_copy;

@@ -16,8 +16,9 @@ component labels). A scheduler thread runs the loop:
              moment form the next launch unit: up to ``max_batch`` small jobs of
              one kind (at most ``small_cutoff`` elements) are concatenated and
              ranked or labelled by one batched launch (``lr_rank_batched_sized``,
-             ``cc_label_batched``); a larger job is launched alone
-             (``lr_rank``, ``cc_label``);
+             ``cc_label_batched``); a larger job, or a small job that finds no
+             other of its kind waiting, is launched alone (``lr_rank``,
+             ``cc_label``);
 * overlap    every unit runs on its own stream, so units admitted while others
              are on the GPU execute concurrently; inputs are copied in and
              results copied out on the unit's stream;
@@ -169,7 +170,7 @@ class Server:
     # ---------------------------------------------------------- internals
     def _unit_ws(self, jobs: list) -> int:
         """Kernel workspace the library needs for this launch unit."""
-        if len(jobs) == 1 and jobs[0].n > self.small_cutoff:
+        if len(jobs) == 1:
             j = jobs[0]
             return workspace_query(KIND_LR, j.n) if j.kind == LIST else workspace_query(KIND_CC, j.n, j.m)
         if jobs[0].kind == LIST:
@@ -230,7 +231,9 @@ class Server:
                 self.ws_cap[slot] += held - self.ws_bytes
                 self.ws_bytes = held
         with torch.cuda.stream(stream):
-            if len(jobs) == 1 and jobs[0].n > self.small_cutoff:
+            if len(jobs) == 1:
+                # a job alone takes the single-instance call, which spreads it over
+                # the whole GPU (the batched kernel gives each instance one block)
                 j = jobs[0]
                 out = torch.empty(j.n, dtype=torch.int32, device=dev)
                 if j.kind == LIST:

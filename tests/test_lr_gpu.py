@@ -190,10 +190,10 @@ def test_overflow_pool_carries_long_sublists():
 
 
 @pytest.mark.parametrize("n", [(1 << 16) + 1, (1 << 17) + 5, 3 * (1 << 20) + 7, (1 << 24) - 3])
-def test_read_only_level_window_placement(n):
-    # the read-only first level places ranks through shared-memory windows once a
-    # bucket's window holds at least 64 ranks: windows of 2^6 .. 2^13 here, with
-    # a partial last bucket and windows wholly past n; closed form of the layout
+def test_read_only_level_ragged_sizes(n):
+    # the read-only first level (chunks, bucket scatter, placement) on sizes that
+    # leave the last id bucket partial; closed form of the random layout, and the
+    # ordered layout, whose walks fill few buckets at a time
     base = lrcc.get_plan(lrcc.KIND_LR, n)
     try:
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_level0=2)
@@ -210,9 +210,9 @@ def test_read_only_level_window_placement(n):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("n", [(1 << 26) + 12345, (1 << 27) + 777])
-def test_read_only_level_512_and_1024_buckets(n):
-    # lists of 2^26 .. 2^27 elements take 512 coarse buckets, up to 2^28 take 1024
-    # (2^18 ids each, cut into eight windows of 2^15 ranks); random and ordered layouts
+def test_read_only_level_large_ragged(n):
+    # the default plan's read-only first level between the powers of two the
+    # bench uses: random and ordered layouts, closed forms
     succ, head, perm = gen.list_random(n, 5, with_perm=True)
     t = torch.from_numpy(succ).to(DEV)
     rank = lrcc.lr_rank(t, head)

@@ -566,19 +566,16 @@ __global__ void __launch_bounds__(SEG_BLOCK)
                 nkeep += active;
             }
             if (compact) {
-                int incl = nkeep;
+                int total = 0;
+                const int excl = warp_prefix_small(nkeep, &total);
+                if (total > 0) {   // warp-uniform
+                    if (staged + total > SEG_STAGE) flush();
+                    int at = staged + excl;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
+                    for (int q = 0; q < SEG_RUN; ++q)
+                        if (u[q] >= 0) stage[at++] = make_int2(u[q], v[q]);
+                    staged += total;
                 }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (staged + total > SEG_STAGE) flush();
-                int at = staged + incl - nkeep;
-#pragma unroll
-                for (int q = 0; q < SEG_RUN; ++q)
-                    if (u[q] >= 0) stage[at++] = make_int2(u[q], v[q]);
-                staged += total;
             }
         }
     }

@@ -159,19 +159,16 @@ __global__ void __launch_bounds__(BLOCK, 6)
             ok[q] = active;
         }
         if (compact) {
-            int incl = keep_cnt;
+            int total = 0;
+            const int excl = warp_prefix_small(keep_cnt, &total);
+            if (total > 0) {   // warp-uniform; most iterations keep nothing
+                if (staged + total > CC_STAGE) flush();
+                int at = staged + excl;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
+                for (int q = 0; q < 4; ++q)
+                    if (ok[q]) stage[at++] = make_int2(u[q], v[q]);
+                staged += total;
             }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (staged + total > CC_STAGE) flush();
-            int at = staged + incl - keep_cnt;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (ok[q]) stage[at++] = make_int2(u[q], v[q]);
-            staged += total;
         }
     }
     if (compact && staged > 0) flush();

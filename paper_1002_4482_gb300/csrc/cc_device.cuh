@@ -69,4 +69,20 @@ __device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b,
     }
 }
 
+// Exclusive prefix over the warp of a per-lane count in [0, 15], and the warp
+// total, from four ballots (one per bit) instead of a shuffle scan: ballots do
+// not queue on the memory pipe that the gathers of a hook pass keep busy.
+__device__ __forceinline__ int warp_prefix_small(int cnt, int* total) {
+    const unsigned lt = lanemask_lt();
+    int excl = 0, all = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, (cnt >> b) & 1);
+        excl += __popc(m & lt) << b;
+        all += __popc(m) << b;
+    }
+    *total = all;
+    return excl;
+}
+
 }  // namespace lrcc

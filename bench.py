@@ -789,6 +789,40 @@ def main():
     step_stats = {"runs": len(per_step), "median_ms": (per_step[9] + per_step[10]) / 2, "min_ms": per_step[0],
                   "max_ms": per_step[-1]}
 
+    # the two halves of the step are independent: the same step with the list on
+    # one stream and the graph on another (each with its own workspace), joined
+    # on the launching stream; K steps, CUDA events on the launching stream
+    s_lr, s_cc = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def step_two_streams():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        s_lr.wait_event(ev)
+        s_cc.wait_event(ev)
+        lrcc.lr_rank(succ, head, out=rank_out, stream=s_lr)
+        lrcc.cc_label(src, dst, n_cc, out=label, stream=s_cc)
+        for s_ in (s_lr, s_cc):
+            e = torch.cuda.Event()
+            e.record(s_)
+            stream.wait_event(e)
+
+    for _ in range(args.warmup):
+        step_two_streams()
+    stream.synchronize()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for _ in range(args.steps):
+        step_two_streams()
+    t1e.record(stream)
+    stream.synchronize()
+    lrcc.check(s_lr)
+    lrcc.check(s_cc)
+    step_stats["two_streams_ms"] = t0e.elapsed_time(t1e) / args.steps
+    step_stats["two_streams_note"] = ("lr_rank and cc_label on two streams of their own, joined each step; the "
+                                      "headline value keeps them one after the other on one stream")
+    lrcc.release(s_lr)
+    lrcc.release(s_cc)
+
     # second timed pass of K steps with the library's phase timing on: CUDA
     # events on the launching stream around every kernel (plain launches),
     # for the per-kernel durations behind the roofline and the phase split

@@ -919,6 +919,35 @@ def main():
                         "frac": steps_per_s / gather,
                         "note": "each walk step is one dependent random read of succ; HBM row activations, "
                                 "not bytes, bound random access"}}
+        # the other kernels of the step, each against the bound that applies to it
+        others = []
+
+        def kernel_row(name, phase, bytes_, note, ceiling=None):
+            if phase not in phases:
+                return
+            ms = phases[phase][0] / phases[phase][1]
+            row = {"kernel": name, "ms_per_launch": ms, "algorithmic_bytes": bytes_,
+                   "achieved_gbs": bytes_ / (ms / 1e3) / 1e9, "frac_of_hbm": bytes_ / (ms / 1e3) / 1e9 / hbm,
+                   "note": note}
+            if ceiling:
+                row.update(ceiling)
+            others.append(row)
+
+        if level0 == 2:
+            kernel_row("rs_scatter", "rs_scatter", 13 * n_lr,
+                       "5 B read (chunk id + header) + 8 B pair written per element; bound by its shared-memory "
+                       "bucket sort")
+            kernel_row("rs_place", "rs_expand0", 12 * n_lr,
+                       "8 B pair read + 4 B rank written per element; bound by L2 requests (one per random rank "
+                       "write)")
+        others.append({"kernel": "cc_hook (first pass over all edges)", "ms_per_launch": full_pass_ms,
+                       "algorithmic_bytes": 16 * m_cc,
+                       "achieved_gbs": 16 * m_cc / (full_pass_ms / 1e3) / 1e9,
+                       "frac_of_hbm": 16 * m_cc / (full_pass_ms / 1e3) / 1e9 / hbm,
+                       "ceiling_ms": probe_ms, "frac_of_ceiling": probe_ms / full_pass_ms,
+                       "note": "8 B edge + two 4-byte parent gathers per edge; ceiling: the gather probe (same "
+                               "edge stream and gathers, no hooking), bound by the SM-to-L2 request port"})
+        roofline["other_kernels"] = others
 
     # ordered control and Wyllie baseline on the same list size (not part of the step)
     extra = {}

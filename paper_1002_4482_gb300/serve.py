@@ -107,6 +107,7 @@ class Server:
             self.ctx.reserve(st, 0)
         self.ws_bytes = self.ctx.bytes()           # bytes the library context holds (all streams)
         self.ws_cap = [0] * streams                # kernel workspace bytes each stream holds
+        self.peak = self.ws_bytes                  # largest resident job bytes + workspace seen
         self.pending: collections.deque[Job] = collections.deque()
         self.inflight: list[_Unit] = []
         self.used = 0
@@ -165,7 +166,7 @@ class Server:
         elems = sum(j.n + j.m for j in jobs)
         return {"jobs": len(jobs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "jobs_per_s": len(jobs) / span, "melems_per_s": elems / span / 1e6,
-                "errors": self.errors, "workspace_bytes": self.ws_bytes}
+                "errors": self.errors, "workspace_bytes": self.ws_bytes, "peak_device_bytes": self.peak}
 
     # ---------------------------------------------------------- internals
     def _unit_ws(self, jobs: list) -> int:
@@ -230,6 +231,7 @@ class Server:
             with self.lock:
                 self.ws_cap[slot] += held - self.ws_bytes
                 self.ws_bytes = held
+                self.peak = max(self.peak, self.used + self.ws_bytes)
         with torch.cuda.stream(stream):
             if len(jobs) == 1:
                 # a job alone takes the single-instance call, which spreads it over
@@ -302,6 +304,7 @@ class Server:
         with self.lock:
             self.ws_cap[u.slot] += held - self.ws_bytes
             self.ws_bytes = held
+            self.peak = max(self.peak, self.used + self.ws_bytes)
             self.used -= u.bytes
             self.busy[u.slot] = False
             self.done.extend(u.jobs)
@@ -329,6 +332,7 @@ class Server:
                     jobs, need = picked
                     self.busy[slot] = True
                     self.used += sum(j.device_bytes() for j in jobs)
+                    self.peak = max(self.peak, self.used + self.ws_bytes)
                     launches.append((jobs, slot, need))
                 if not launches and not self.inflight and not self.stop_flag:
                     self.wake.wait(timeout=0.01)

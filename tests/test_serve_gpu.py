@@ -94,6 +94,27 @@ def test_admission_under_tiny_budget_and_fifo_reference():
         assert np.array_equal(x, expect) and np.array_equal(y, expect)
 
 
+def test_workspace_is_reserved_counted_and_freed_through_a_context():
+    # the server reserves its streams' workspaces through a library context and
+    # counts them against its budget; closing it frees them
+    jobs = _make_jobs(24, 3, lo=12, hi=19)
+    before = lrcc.workspace_bytes()
+    budget = 96 << 20
+    srv = serve.Server(0, mem_budget=budget, streams=2, small_cutoff=1 << 14, max_batch=16)
+    try:
+        results = _run_mix(srv, jobs, seed=9)
+        srv.drain(60)
+        st = srv.stats()
+        held = srv.ctx.bytes()
+    finally:
+        srv.close()
+    for j, r in zip(jobs, results):
+        assert np.array_equal(r, j[3] if j[0] == "list" else j[4])
+    assert st["workspace_bytes"] == held and held > 0
+    assert st["peak_device_bytes"] <= budget
+    assert lrcc.workspace_bytes() == before
+
+
 def test_invalid_job_fails_only_its_unit():
     srv = serve.Server(0, streams=2, small_cutoff=1 << 10)
     try:

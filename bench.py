@@ -93,7 +93,8 @@ def run_case(argv):
     what, log2 = argv[0], int(argv[1])
     variant = argv[2] if len(argv) > 2 else ""
     dev = torch.device("cuda:0")
-    for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC, lrcc.KIND_LR_BATCH, lrcc.KIND_CC_BATCH):
+    for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC, lrcc.KIND_CC_SPARSE, lrcc.KIND_LR_BATCH,
+                 lrcc.KIND_CC_BATCH):
         lrcc.set_plan(kind, 0, 32, use_graphs=2)
     level0 = {"inplace": 1, "readonly": 2, "split": 3}
     if variant in level0:
@@ -501,7 +502,7 @@ def bench_families(lrcc, torch, dev, stream, m=8_000_000):
         row = {"family": kind, "k": k, "density": d, "n": n, "m": len(src)}
         ref = None
         for name, hook in (("atomicmin", base["cc_hook"]), ("shiloach_vishkin", 4)):
-            lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=hook)
+            lrcc.set_cc_plan(0, 32, cc_hook=hook)
             lrcc.cc_label(S, D, n, out=lab, stream=stream)
             stream.synchronize()
             best = float("inf")
@@ -518,7 +519,7 @@ def bench_families(lrcc, torch, dev, stream, m=8_000_000):
                 ref = lab.clone()
             elif not torch.equal(ref, lab):
                 raise AssertionError(f"hook rules disagree on {kind} {k} {d}")
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=base["cc_hook"])
+        lrcc.reset_plans()
         row["sv_round_bound"] = int(math.floor(math.log(n) / math.log(1.5))) + 2
         out.append(row)
         del S, D, lab, ref
@@ -723,7 +724,7 @@ def main():
         return ranks.max_over_ranks(x, dev)
 
     if args.plain_launches:
-        for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC):
+        for kind in (lrcc.KIND_LR, lrcc.KIND_LR_WYLLIE, lrcc.KIND_CC, lrcc.KIND_CC_SPARSE):
             lrcc.set_plan(kind, 0, 32, use_graphs=2)
     succ_h, head, src_h, dst_h, n_cc, cfg = workload(args.workload)
     n_lr, m_cc = len(succ_h), len(src_h)
@@ -868,7 +869,7 @@ def main():
     # the first pass over all edges alone: one call with plain launches (the host
     # drives the loop, so each pass is its own launch) and phase timing on
     cc_graphs = lrcc.get_plan(lrcc.KIND_CC, n_cc)["use_graphs"]
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=2)
+    lrcc.set_cc_plan(0, 32, use_graphs=2)
     lrcc.set_timing(True)
     lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
     lrcc.phase_times(stream)
@@ -877,7 +878,7 @@ def main():
         lrcc.cc_label(src, dst, n_cc, out=label, stream=stream)
         full_pass.append(lrcc.phase_times(stream).get("cc_hook_full", (float("nan"), 0))[0])
     lrcc.set_timing(False)
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=cc_graphs)
+    lrcc.set_cc_plan(0, 32, use_graphs=cc_graphs)
     lrcc.check(stream)
     full_pass_ms = min(full_pass)
 

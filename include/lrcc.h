@@ -309,8 +309,10 @@ typedef struct lrcc_plan {
                                 at least 8 edges per vertex, two with 4 to 7, no sample below) */
 } lrcc_plan;
 
-/* kind: 1 = list ranking, 3 = connected components; sizes with ceil(log2 n)
- * in [log2_lo, log2_hi] get `plan`. */
+/* kind: 1 = list ranking, 2 = its Wyllie form, 3 = connected components of
+ * graphs with at least 4 edges per vertex, 8 = connected components of graphs
+ * with fewer (m < 4n), 4 / 5 = the batched calls; sizes with ceil(log2 n) in
+ * [log2_lo, log2_hi] get `plan`. */
 lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* plan);
 lrcc_status lrcc_get_plan(int kind, int64_t n, lrcc_plan* out);
 /* Restores the built-in plan table (undoing every lrcc_set_plan). */

@@ -28,6 +28,7 @@ _lib = None
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_INVALID_INPUT, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(7)
 KIND_LR, KIND_LR_WYLLIE, KIND_CC, KIND_LR_BATCH, KIND_CC_BATCH = 1, 2, 3, 4, 5
+KIND_CC_SPARSE = 8   # plan class of graphs with fewer than 4 edges per vertex
 
 SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label",
            "lr_rank_host", "cc_label_host", "lr_scan", "lr_scan_forest",
@@ -360,6 +361,13 @@ def last_stats(stream=None) -> dict:
 def set_plan(kind: int, log2_lo: int = 0, log2_hi: int = 32, **fields) -> None:
     p = Plan(**fields)
     _call(load().lrcc_set_plan(kind, log2_lo, log2_hi, ctypes.byref(p)), "lrcc_set_plan")
+
+
+def set_cc_plan(log2_lo: int = 0, log2_hi: int = 32, **fields) -> None:
+    """Plan fields for every components call: graphs with at least 4 edges per
+    vertex (KIND_CC) and with fewer (KIND_CC_SPARSE) alike."""
+    set_plan(KIND_CC, log2_lo, log2_hi, **fields)
+    set_plan(KIND_CC_SPARSE, log2_lo, log2_hi, **fields)
 
 
 def reset_plans() -> None:

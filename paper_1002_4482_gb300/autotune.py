@@ -17,7 +17,8 @@ counts, so a wrong plan can never win:
 Knobs searched:
   lists       first-level mode (in-place words / read-only walk), spacing at the
               first and deeper levels, walks per thread, one-block cutoff
-  components  hook rule (single hook / re-link / single then re-link), sample pass size
+  components  hook rule (single hook / re-link / single then re-link), sample pass size, for
+              graphs with at least 4 edges per vertex and, apart, for sparser ones
   batched     minimum splitter spacing of in-block ruling sets; hook rule of the
               large-graph union path
 
@@ -38,8 +39,8 @@ import time
 import numpy as np
 import torch
 
-from . import (KIND_CC, KIND_CC_BATCH, KIND_LR, KIND_LR_BATCH, cc_label, cc_label_batched, check, get_plan,
-               lr_rank, lr_rank_batched, set_plan)
+from . import (KIND_CC, KIND_CC_BATCH, KIND_CC_SPARSE, KIND_LR, KIND_LR_BATCH, cc_label, cc_label_batched, check,
+               get_plan, lr_rank, lr_rank_batched, set_plan)
 
 
 def _timeit(fn, stream, reps=3):
@@ -124,19 +125,30 @@ def _reference_labels(kind, log2_lo, log2_hi, run):
         set_plan(kind, log2_lo, log2_hi, **{k: saved[k] for k in ("cc_hook", "cc_sample", "use_graphs")})
 
 
-def tune_graphs(classes=(16, 20, 24), device=0, log=print):
+def tune_graphs(classes=(16, 20, 24), device=0, log=print, sparse=False):
+    """Hook rule and sample pass per size class. Dense (KIND_CC): R-MAT graphs
+    of 16 edges per vertex and uniform random graphs of 4; sparse
+    (KIND_CC_SPARSE, fewer than 4 edges per vertex): uniform random graphs of 2
+    and collections of paths."""
     import gen
     from gen import workloads
     dev = torch.device("cuda", device)
     stream = torch.cuda.Stream(dev)
+    kind = KIND_CC_SPARSE if sparse else KIND_CC
     results = {}
     for c, lo, hi in _ranges(classes):
-        # a mix of the two graph families the library is measured on
-        src1, dst1, n1 = workloads.cc_rmat(c, 16, seed=200 + c)
-        src2, dst2 = gen.er(1 << c, 1 << (c + 2), 300 + c)
+        if sparse:
+            src1, dst1 = gen.er(1 << c, 1 << (c + 1), 400 + c)
+            n1 = 1 << c
+            src2, dst2, n2 = gen.list_graph(16, (1 << c) // 16, 500 + c)
+        else:
+            # a mix of the two graph families the library is measured on
+            src1, dst1, n1 = workloads.cc_rmat(c, 16, seed=200 + c)
+            src2, dst2 = gen.er(1 << c, 1 << (c + 2), 300 + c)
+            n2 = 1 << c
         cases = []
         with torch.cuda.stream(stream):
-            for s_, d_, n_ in ((src1, dst1, n1), (src2, dst2, 1 << c)):
+            for s_, d_, n_ in ((src1, dst1, n1), (src2, dst2, n2)):
                 cases.append((torch.from_numpy(s_).to(dev), torch.from_numpy(d_).to(dev), n_,
                               torch.empty(n_, dtype=torch.int32, device=dev), s_, d_))
         expect = []
@@ -146,10 +158,10 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print):
                 stream.synchronize()
                 check(stream)
                 return lab
-            expect.append(_reference_labels(KIND_CC, c, c, run))
+            expect.append(_reference_labels(kind, c, c, run))
         best = None
         for hook, samp in itertools.product((1, 2, 3), (-1, 1, 4, 8)):
-            set_plan(KIND_CC, c, c, cc_hook=hook, cc_sample=samp, use_graphs=1)
+            set_plan(kind, c, c, cc_hook=hook, cc_sample=samp, use_graphs=1)
             ms = 0.0
             for (sd, dd, n_, lab, _, _), want in zip(cases, expect):
                 ms += _timeit(lambda: cc_label(sd, dd, n_, out=lab, stream=stream), stream)
@@ -160,9 +172,9 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print):
                                          f"plan's at 2^{c}")
             if best is None or ms < best[0]:
                 best = (ms, {"cc_hook": hook, "cc_sample": samp})
-        set_plan(KIND_CC, lo, hi, **best[1])
+        set_plan(kind, lo, hi, **best[1])
         results[str(c)] = {"range": [lo, hi], "ms": best[0], "plan": best[1]}
-        log(f"graphs 2^{c}: {best[0]:.3f} ms with {best[1]}")
+        log(f"{'sparse ' if sparse else ''}graphs 2^{c}: {best[0]:.3f} ms with {best[1]}")
     return results
 
 
@@ -228,6 +240,7 @@ def tune(quick=False, device=0, log=print, list_classes=(16, 20, 24, 28), graph_
     out = {"gpu": torch.cuda.get_device_name(device), "quick": quick,
            "lists": tune_lists(list_classes, quick, device, log),
            "graphs": tune_graphs(graph_classes, device, log),
+           "sparse_graphs": tune_graphs(graph_classes, device, log, sparse=True),
            "batched": tune_batched(batch_log2, device, log)}
     out["seconds"] = time.time() - t0
     return out
@@ -239,6 +252,8 @@ def apply(result: dict) -> None:
         set_plan(KIND_LR, entry["range"][0], entry["range"][1], **entry["plan"])
     for entry in result.get("graphs", {}).values():
         set_plan(KIND_CC, entry["range"][0], entry["range"][1], **entry["plan"])
+    for entry in result.get("sparse_graphs", {}).values():
+        set_plan(KIND_CC_SPARSE, entry["range"][0], entry["range"][1], **entry["plan"])
     b = result.get("batched", {})
     if "lists" in b:
         set_plan(KIND_LR_BATCH, 0, 32, **b["lists"]["plan"])

@@ -20,6 +20,12 @@ constexpr int KIND_LR_WYLLIE = 2;
 constexpr int KIND_CC = 3;
 constexpr int KIND_LR_BATCH = 4;
 constexpr int KIND_CC_BATCH = 5;
+// Plan class of graphs with fewer than 4 edges per vertex (m < 4n); 6 and 7
+// name the weighted-rank calls in statistics and workspace queries.
+constexpr int KIND_CC_SPARSE = 8;
+constexpr int PLAN_KINDS = 9;
+// Plan class of a components call: sparse graphs are planned apart.
+inline int cc_plan_kind(int64_t m, int64_t n) { return (n > 0 && m < 4 * n) ? KIND_CC_SPARSE : KIND_CC; }
 
 // Resolved tuning knobs (every field set).
 struct Plan {

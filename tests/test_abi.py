@@ -70,7 +70,7 @@ def test_status_strings(lib):
     assert lrcc.status_str(0) == "ok"
     assert "invalid input" in lrcc.status_str(4)
     assert lrcc.status_str(99) == "unknown status"
-    assert lrcc.load().lrcc_version() == 100
+    assert lrcc.load().lrcc_version() == 101
 
 
 def test_host_side_argument_errors_need_no_gpu(lib):
@@ -110,9 +110,28 @@ def test_plan_table_roundtrip(lib):
         lrcc.set_plan(lrcc.KIND_CC, 20, 20, cc_hook=before)
 
 
+def test_sparse_graphs_have_their_own_plan_class(lib):
+    lrcc.reset_plans()
+    # built in: re-linking after a sample pass once a sparse graph's parent array outgrows L2
+    assert lrcc.get_plan(lrcc.KIND_CC_SPARSE, 1 << 26)["cc_hook"] == 3
+    assert lrcc.get_plan(lrcc.KIND_CC_SPARSE, 1 << 26)["cc_sample"] == 8
+    assert lrcc.get_plan(lrcc.KIND_CC, 1 << 26)["cc_hook"] == 1
+    assert lrcc.get_plan(lrcc.KIND_CC_SPARSE, 1 << 20) == lrcc.get_plan(lrcc.KIND_CC, 1 << 20)
+    # the workspace query takes the class from the edges per vertex
+    L = lrcc.load()
+    lrcc.set_plan(lrcc.KIND_CC_SPARSE, 20, 20, cc_hook=4)
+    try:
+        assert L.lrcc_workspace_query(lrcc.KIND_CC, 1 << 20, 3 << 20) == 4 * (1 << 20)   # 3 edges per vertex
+        assert L.lrcc_workspace_query(lrcc.KIND_CC, 1 << 20, 1 << 22) != 4 * (1 << 20)   # 4 per vertex: dense
+    finally:
+        lrcc.reset_plans()
+    with pytest.raises(lrcc.LrccError):
+        lrcc.set_plan(6, 0, 32, cc_hook=1)
+
+
 def test_reset_plans_restores_the_builtin_table(lib):
     lrcc.reset_plans()
-    before = {k: lrcc.get_plan(k, 1 << 24) for k in (lrcc.KIND_LR, lrcc.KIND_CC, lrcc.KIND_LR_BATCH)}
+    before = {k: lrcc.get_plan(k, 1 << 24) for k in (lrcc.KIND_LR, lrcc.KIND_CC, lrcc.KIND_CC_SPARSE, lrcc.KIND_LR_BATCH)}
     lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_spacing0=128, rs_level0=2, seed=7)
     lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=4, cc_sample=3)
     lrcc.reset_plans()

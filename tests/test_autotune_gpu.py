@@ -25,6 +25,7 @@ def test_quick_tune_installs_checked_plans(tmp_path):
         path.write_text(json.dumps(res))
         assert autotune.load(str(path))
         assert lrcc.get_plan(lrcc.KIND_LR, 1 << 18)["rs_spacing0"] == res["lists"]["18"]["plan"]["rs_spacing0"]
+        assert lrcc.get_plan(lrcc.KIND_CC_SPARSE, 1 << 14)["cc_hook"] == res["sparse_graphs"]["14"]["plan"]["cc_hook"]
         # results under the tuned plans are still exact
         succ, head = gen.list_random(200_000, 5)
         r = lrcc.lr_rank(torch.from_numpy(succ).to(DEV), head).cpu().numpy()

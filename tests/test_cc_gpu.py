@@ -25,10 +25,9 @@ def _run(src, dst, n):
 
 @pytest.fixture(params=[1, 2, 3, 4], ids=["hook-once", "hook-relink", "hook-once-then-relink", "shiloach-vishkin"])
 def hook(request):
-    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 20)["cc_hook"]
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=request.param)
+    lrcc.set_cc_plan(0, 32, cc_hook=request.param)
     yield request.param
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=base)
+    lrcc.reset_plans()
 
 
 @pytest.mark.parametrize("n,m", [(1, 0), (1, 1), (5, 0), (10, 3), (33, 40), (1000, 500), (1000, 3000),
@@ -81,11 +80,11 @@ def test_graphs_off_and_repeated(hook):
     expect = oracle.cc_uf(src, dst, 200_000)
     for _ in range(5):
         assert np.array_equal(_run(src, dst, 200_000), expect)
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=2)
+    lrcc.set_cc_plan(0, 32, use_graphs=2)
     try:
         assert np.array_equal(_run(src, dst, 200_000), expect)
     finally:
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, use_graphs=1)
+        lrcc.set_cc_plan(0, 32, use_graphs=1)
 
 
 def test_unaligned_views():
@@ -114,14 +113,15 @@ def test_round_cap_is_reported():
     # stop with NOT_CONVERGED; the default cap then labels it correctly
     src, dst = gen.er(5000, 4000, 5)
     s, d = torch.from_numpy(src).to(DEV), torch.from_numpy(dst).to(DEV)
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_max_rounds=1)
+    lrcc.set_cc_plan(0, 32, cc_max_rounds=1)
     try:
         lrcc.cc_label(s, d, 5000)
         st = lrcc.last_status()
     finally:
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_max_rounds=-1)
+        lrcc.set_cc_plan(0, 32, cc_max_rounds=-1)
     assert st == lrcc.ERR_NOT_CONVERGED
     assert lrcc.get_plan(lrcc.KIND_CC, 5000)["cc_max_rounds"] == 0
+    assert lrcc.get_plan(lrcc.KIND_CC_SPARSE, 5000)["cc_max_rounds"] == 0
     assert np.array_equal(_run(src, dst, 5000), oracle.cc_uf(src, dst, 5000))
 
 
@@ -131,8 +131,7 @@ def test_sample_pass_keeps_labels(hook, sample):
     # whatever the prefix holds: dense random graphs, many small components, a
     # prefix that already holds every edge (the list repeated), and a long path
     # whose prefix is one piece of it
-    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 16)["cc_sample"]
-    lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=sample)
+    lrcc.set_cc_plan(0, 32, cc_sample=sample)
     try:
         src, dst = gen.er(1 << 16, 1 << 20, 41)           # 16 edges per vertex
         assert np.array_equal(_run(src, dst, 1 << 16), oracle.cc_uf(src, dst, 1 << 16))
@@ -149,22 +148,20 @@ def test_sample_pass_keeps_labels(hook, sample):
         src, dst, n = workloads.cc_rmat(16, 16)
         assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
     finally:
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=base)
+        lrcc.set_cc_plan(0, 32, cc_hook=hook, cc_sample=-1)
 
 
 def test_stats_count_edges_read():
     # no sample pass: the first pass reads every edge, each later pass at most all of them;
     # with the sample pass of m/16 edges, that prefix is read once more
     src, dst = gen.er(1 << 16, 1 << 20, 45)
-    base = lrcc.get_plan(lrcc.KIND_CC, 1 << 16)["cc_sample"]
     try:
         for sample, extra in ((1, 0), (16, (1 << 20) // 16)):
-            lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=sample, cc_hook=1)
+            lrcc.set_cc_plan(0, 32, cc_sample=sample, cc_hook=1)
             assert np.array_equal(_run(src, dst, 1 << 16), oracle.cc_uf(src, dst, 1 << 16))
             st = lrcc.last_stats()
             assert (1 << 20) + extra <= st["edges_read"] <= st["rounds"] * (1 << 20) + extra, (sample, st)
     finally:
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=base)
         lrcc.reset_plans()
 
 
@@ -212,3 +209,15 @@ def test_gather_probe_reads_every_endpoint():
     lrcc.check()
     want = int(table[src].astype(np.int64).sum() + table[dst].astype(np.int64).sum())
     assert int(got.item()) == want
+
+
+@pytest.mark.slow
+def test_large_sparse_graph_takes_its_plan_class():
+    # 2^24 + 1000 vertices, 2 edges per vertex: the sparse class's built-in plan
+    # for 2^25 (re-linking after a sample pass) against union-find
+    n = (1 << 24) + 1000
+    src, dst = gen.er(n, 2 * n, 71)
+    assert lrcc.get_plan(lrcc.KIND_CC_SPARSE, n)["cc_hook"] == 3
+    assert np.array_equal(_run(src, dst, n), oracle.cc_uf(src, dst, n))
+    src, dst, n2 = gen.list_graph(64, (1 << 24) // 64 + 3, 72)     # long paths: many passes
+    assert np.array_equal(_run(src, dst, n2), oracle.cc_uf(src, dst, n2))

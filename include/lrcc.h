@@ -262,6 +262,15 @@ lrcc_status lrcc_wait_check(int polls, void* stream);
 lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m, const int32_t* table, int64_t n,
                               int64_t* out, void* stream);
 
+/*
+ * Fault injection on the host, for testing a caller's out-of-memory handling:
+ * the next `count` device allocations the library makes (workspaces, host-call
+ * staging) fail as if cudaMalloc had, and the calls that needed them return
+ * LRCC_ERR_NOMEM without enqueueing work. count <= 0 clears it. Returns the
+ * count that was pending. Nothing is done on the device.
+ */
+int lrcc_debug_fail_allocs(int count);
+
 /* Statistics of the most recent call on `stream` (waits for the stream). */
 typedef struct lrcc_stats {
     int32_t kind;            /* 1 = lr_rank, 2 = lr_rank_wyllie, 3 = cc_label, 4/5 = batched,

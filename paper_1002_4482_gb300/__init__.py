@@ -37,7 +37,7 @@ SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_r
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity",
            "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_bytes", "lrcc_ctx_last_status", "lrcc_ctx_destroy",
-           "lrcc_gather_probe", "lr_rank_splitters")
+           "lrcc_gather_probe", "lr_rank_splitters", "lrcc_debug_fail_allocs")
 
 
 class LrccError(RuntimeError):
@@ -115,6 +115,8 @@ def load() -> ctypes.CDLL:
         lib.lrcc_ctx_destroy.restype = None
         lib.lrcc_gather_probe.argtypes = [p, p, i64, p, i64, p, p]
         lib.lr_rank_splitters.argtypes = [p, i64, i32, p, i64, p, p]
+        lib.lrcc_debug_fail_allocs.argtypes = [i]
+        lib.lrcc_debug_fail_allocs.restype = i
         for f in ("lr_rank", "lr_rank_wyllie", "lr_rank_noalloc", "cc_label", "lr_rank_host", "cc_label_host",
                   "lr_scan", "lr_scan_forest",
                   "lr_rank_batched",
@@ -404,6 +406,12 @@ def gather_probe(src: torch.Tensor, dst: torch.Tensor, table: torch.Tensor, stre
     _call(load().lrcc_gather_probe(src.data_ptr(), dst.data_ptr(), src.numel(), table.data_ptr(), table.numel(),
                                    out.data_ptr(), _stream(stream)), "lrcc_gather_probe")
     return out
+
+
+def debug_fail_allocs(count: int) -> int:
+    """Make the library's next `count` device allocations fail (ERR_NOMEM), for
+    testing out-of-memory handling; returns the count that was pending."""
+    return int(load().lrcc_debug_fail_allocs(int(count)))
 
 
 def set_timing(enable: bool) -> None:

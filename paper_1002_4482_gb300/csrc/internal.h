@@ -57,7 +57,6 @@ struct RsLayout {
     bool split = false;             // level 0 over split mark / local-rank arrays
     int64_t grid = 0, cap = 0, ovf_cap = 0;
     int segcap = 0, units = 0;
-    int nb_log = 8;                 // coarse id buckets of the scatter: 2^nb_log
     size_t off_ids = 0, off_meta = 0, off_fill = 0, off_counts = 0, off_totals = 0,
         off_vis = 0;
     size_t bytes = 0;

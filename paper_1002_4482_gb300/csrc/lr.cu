@@ -370,8 +370,8 @@ struct Chunks {
     int32_t* ids;        // chunk c: ids[8c .. 8c+8), unused slots -1
     uint64_t* meta;      // meta[c] = k0 << 32 | j
     int* fill;           // chunks written into each block's own region
-    int* counts;         // [nb][units] elements per (bucket, scatter unit); then row offsets
-    int* totals;         // [nb] elements per bucket
+    int* counts;         // [NBK][units] elements per (bucket, scatter unit); then row offsets
+    int* totals;         // [NBK] elements per bucket
     uint32_t* vis;       // careful-mode marks, one bit per element
     int64_t cap;         // chunks per block region (NSEG segments of segcap)
     int segcap;          // chunks per segment (even); a segment is one scatter work unit
@@ -379,7 +379,6 @@ struct Chunks {
     int64_t ovf_cap;     // overflow chunks
     int64_t ovf_base;    // index of the first overflow chunk (= grid * cap)
     int shift;           // coarse bucket of element x = x >> shift
-    int nb;              // coarse buckets (NBK)
     int64_t careful;     // steps after which a walk marks what it visits
 };
 
@@ -418,8 +417,8 @@ __global__ void __launch_bounds__(BLOCK)
     }
     constexpr int WCHUNK = 64;
     __shared__ int s_fill;
-    __shared__ int s_cnt[NSEG * NBK];   // [segment][bucket], nb buckets per segment
-    for (int t = threadIdx.x; t < NSEG * C.nb; t += BLOCK) s_cnt[t] = 0;
+    __shared__ int s_cnt[NSEG][NBK];
+    for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) (&s_cnt[0][0])[t] = 0;
     if (threadIdx.x == 0) s_fill = 0;
     __syncthreads();
     const int64_t r = L0.nb + (L0.extra_count ? *L0.extra_count : 0);
@@ -534,7 +533,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
                     for (int t = 0; t < CIDS; ++t)
                         if (t < bn[q]) {
-                            if (ovf_unit < 0) atomicAdd(&s_cnt[seg * C.nb + (v[t] >> C.shift)], 1);
+                            if (ovf_unit < 0) atomicAdd(&s_cnt[seg][v[t] >> C.shift], 1);
                             else atomicAdd(&C.counts[(int64_t)(v[t] >> C.shift) * C.units + ovf_unit], 1);
                         }
                 }
@@ -552,15 +551,15 @@ __global__ void __launch_bounds__(BLOCK)
     }
     __syncthreads();
     if (threadIdx.x == 0) C.fill[blockIdx.x] = min(s_fill, (int)C.cap);
-    for (int t = threadIdx.x; t < NSEG * C.nb; t += BLOCK) {
-        const int bk = t % C.nb, seg = t / C.nb;
-        C.counts[(int64_t)bk * C.units + (int64_t)blockIdx.x * NSEG + seg] = s_cnt[t];
+    for (int t = threadIdx.x; t < NSEG * NBK; t += BLOCK) {
+        const int bk = t % NBK, seg = t / NBK;
+        C.counts[(int64_t)bk * C.units + (int64_t)blockIdx.x * NSEG + seg] = s_cnt[seg][bk];
     }
 }
 
 // Exclusive scan of each bucket's row of per-block counts, in place, one
 // block per bucket; the row total goes to totals[bucket]. The start of each
-// bucket (a scan over the nb totals) is formed by the scatter blocks themselves.
+// bucket (a scan over NBK totals) is formed by the scatter blocks themselves.
 constexpr int SCAN_THREADS = 256;
 __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int G, int* totals) {
     __shared__ int s_warp[SCAN_THREADS / 32];
@@ -615,19 +614,19 @@ constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
 // open suspends the thread for a few microseconds (about 4.3 us measured on
 // GB300), so the limit is about one second.
 constexpr int SC_WAIT_LIMIT = 1 << 18;
-template <int NB>
 struct ScatterSmem {
     int32_t ids[SC_BUF][SC_ITEMS];      // chunk ids of the round in each buffer
     uint64_t meta[SC_BUF][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
     int32_t top[SC_CHUNKS];        // rank of the first element of each chunk
     uint16_t tile[SC_ITEMS];       // slot indices sorted by bucket
-    int cnt[2][NB];                // elements per bucket in the round (alternating)
-    int base[NB];                  // next free pair of each bucket for this region
-    int delta[NB];                 // pair position minus tile slot, per bucket, in the round
-    int tstart[NB];                // start of each bucket's run in the tile
+    int cnt[2][NBK];               // elements per bucket in the round (alternating)
+    int base[NBK];                 // next free pair of each bucket for this region
+    int delta[NBK];                // pair position minus tile slot, per bucket, in the round
+    int tstart[NBK];               // start of each bucket's run in the tile
     int warp[BLOCK / 32];
     uint64_t bar[SC_BUF];
 };
+constexpr size_t SC_SMEM = sizeof(ScatterSmem);
 
 // The 8 ids of one chunk from shared memory. Lanes 4-7 of every 8 read the
 // two 16-byte halves in the other order, so that each quarter-warp phase of
@@ -641,15 +640,12 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int32_t (&id)[CIDS]
     id[4] = hi.x; id[5] = hi.y; id[6] = hi.z; id[7] = hi.w;
 }
 
-// NB buckets (C.nb == NB); thread t owns buckets [t * BPT, (t + 1) * BPT).
-template <int NB>
-__global__ void __launch_bounds__(BLOCK, NB <= 256 ? 4 : 3)
+__global__ void __launch_bounds__(BLOCK, 4)
     rs_scatter(Chunks C, int G, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n,
                DevCtl* ctl) {
     extern __shared__ __align__(128) unsigned char sc_raw[];
-    ScatterSmem<NB>& s = *reinterpret_cast<ScatterSmem<NB>*>(sc_raw);
-    constexpr int BPT = NB / BLOCK;
-    static_assert(NB % BLOCK == 0, "whole buckets per thread");
+    ScatterSmem& s = *reinterpret_cast<ScatterSmem*>(sc_raw);
+    static_assert(NBK == BLOCK, "one thread per bucket");
     static_assert(SC_ITEMS <= 65536, "tile holds 16-bit slot indices");
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     // block-wide exclusive scan of one value per thread (uses s.warp; two syncs)
@@ -673,21 +669,13 @@ __global__ void __launch_bounds__(BLOCK, NB <= 256 ? 4 : 3)
         *total = all;
         return off + incl - v;
     };
-    int bstart[BPT];                // start of each of this thread's buckets in the pair array
+    int bstart;                     // start of bucket t in the pair array
     {
-        int all = 0, mine = 0;
-#pragma unroll
-        for (int k = 0; k < BPT; ++k) mine += C.totals[t * BPT + k];
-        int at = block_scan(mine, &all);
-#pragma unroll
-        for (int k = 0; k < BPT; ++k) {
-            bstart[k] = at;
-            at += C.totals[t * BPT + k];
-        }
+        int all = 0;
+        bstart = block_scan(C.totals[t], &all);
         if (blockIdx.x == 0 && t == 0) ctl->pairs = all;
     }
-#pragma unroll
-    for (int k = 0; k < BPT; ++k) s.cnt[0][t * BPT + k] = s.cnt[1][t * BPT + k] = 0;
+    s.cnt[0][t] = s.cnt[1][t] = 0;
     if (t == 0) {
         for (int b = 0; b < SC_BUF; ++b) mbar_init(&s.bar[b], 1);
         fence_proxy_async_smem();   // the initialised barriers are visible to the bulk copies
@@ -737,23 +725,13 @@ __global__ void __launch_bounds__(BLOCK, NB <= 256 ? 4 : 3)
                 loc[u][q] = (c < cnt && id[q] >= 0) ? atomicAdd(&cntp[id[q] >> C.shift], 1) : 0;
         }
         __syncthreads();
-        int h[BPT], hs = 0;
-#pragma unroll
-        for (int k = 0; k < BPT; ++k) {
-            h[k] = s.cnt[par][t * BPT + k];
-            s.cnt[par ^ 1][t * BPT + k] = 0;   // counts of the next round
-            hs += h[k];
-        }
+        const int h = s.cnt[par][t];
+        s.cnt[par ^ 1][t] = 0;      // counts of the next round
         int items = 0;
-        int ts = block_scan(hs, &items);
-#pragma unroll
-        for (int k = 0; k < BPT; ++k) {
-            const int bk = t * BPT + k;
-            s.tstart[bk] = ts;
-            s.delta[bk] = s.base[bk] - ts;   // pair position of tile slot i of bucket bk: delta[bk] + i
-            s.base[bk] += h[k];
-            ts += h[k];
-        }
+        const int ts = block_scan(h, &items);
+        s.tstart[t] = ts;
+        s.delta[t] = s.base[t] - ts;   // pair position of tile slot i of bucket t: delta[t] + i
+        s.base[t] += h;
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < SC_U; ++u) {
@@ -795,8 +773,7 @@ __global__ void __launch_bounds__(BLOCK, NB <= 256 ? 4 : 3)
             c0 = C.ovf_base + v0;
         }
         if (nf == 0) continue;
-#pragma unroll
-        for (int k = 0; k < BPT; ++k) s.base[t * BPT + k] = bstart[k] + C.counts[(int64_t)(t * BPT + k) * C.units + unit];
+        s.base[t] = bstart + C.counts[(int64_t)t * C.units + unit];
         const int nr = (nf + SC_CHUNKS - 1) / SC_CHUNKS;
         if (t == 0)
             for (int k = 0; k < SC_BUF && k < nr; ++k) issue(c0, nf, k, k);
@@ -1680,7 +1657,6 @@ RsLayout rs_layout(int64_t n, const Plan& p, int walk_grid, int64_t extra1, int6
         L.off_ids = take(sizeof(int32_t) * CIDS * (size_t)chunks);
         L.off_meta = take(sizeof(uint64_t) * (size_t)chunks);
         L.off_fill = take(sizeof(int) * (size_t)G);
-        L.nb_log = NBK_LOG;
         L.off_counts = take(sizeof(int) * (size_t)NBK * (size_t)L.units);
         L.off_totals = take(sizeof(int) * (size_t)NBK);
         L.off_vis = take(sizeof(uint32_t) * (size_t)((n + 31) / 32));
@@ -1835,8 +1811,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     C.ovf_base = L.grid * L.cap;
     int lg = 0;
     while ((int64_t(1) << lg) < n) ++lg;
-    C.nb = 1 << L.nb_log;
-    C.shift = std::max(0, lg - L.nb_log);
+    C.shift = std::max(0, lg - NBK_LOG);
     C.careful = int64_t(32) << L.logD[0];
     auto walk = [&](int l, uint64_t* Wl, int64_t nl) {
         const int r = (int)L.size[l + 1];
@@ -1857,7 +1832,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     if (L.readonly) {
         cudaMemsetAsync(C.vis, 0, sizeof(uint32_t) * (size_t)((n + 31) / 32), s);
         // overflow units' counts are accumulated with atomics (own units are stored whole)
-        cudaMemsetAsync(C.counts, 0, sizeof(int) * (size_t)C.nb * (size_t)L.units, s);
+        cudaMemsetAsync(C.counts, 0, sizeof(int) * (size_t)NBK * (size_t)L.units, s);
         const int G = (int)L.grid;
         phase_begin(c, s);
         if (p.rs_chains >= 4) rs_walk0c<4><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
@@ -1865,7 +1840,7 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
         else rs_walk0c<1><<<G, BLOCK, 0, s>>>(succ, L0, C, R(1), &ctl->work[0], ctl);
         phase_end(c, s, PH_WALK0);
         phase_begin(c, s);
-        rs_scan_counts<<<C.nb, SCAN_THREADS, 0, s>>>(C.counts, L.units, C.totals);
+        rs_scan_counts<<<NBK, SCAN_THREADS, 0, s>>>(C.counts, L.units, C.totals);
         phase_end(c, s, PH_SCAN);
         if (U) {
             phase_begin(c, s);
@@ -1933,11 +1908,9 @@ lrcc_status lr_enqueue_rs(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n
     }
     if (L.readonly) {
         phase_begin(c, s);
-        const void* sk = (const void*)rs_scatter<NBK>;
-        const size_t smem = sizeof(ScatterSmem<NBK>);
-        cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int gs = std::min((int)L.grid, persistent_grid(c, sk, BLOCK, smem));
-        rs_scatter<NBK><<<gs, BLOCK, smem, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
+        cudaFuncSetAttribute((const void*)rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC_SMEM);
+        const int gs = std::min((int)L.grid, persistent_grid(c, (const void*)rs_scatter, BLOCK, SC_SMEM));
+        rs_scatter<<<gs, BLOCK, SC_SMEM, s>>>(C, (int)L.grid, S(1), W0, n, ctl);
         phase_end(c, s, PH_SCATTER);
         phase_begin(c, s);
         rs_place<<<LRCC_PLACE_BLOCKS_PER_SM * c->sms, BLOCK, 0, s>>>(W0, n, rank, ctl);

@@ -10,12 +10,31 @@
 #include <new>
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace lrcc {
 
 namespace {
+
+// A named range around each entry point for tracing tools (NVTX; a no-op
+// unless a tool is attached).
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+};
+
+// Allocation failures injected on the host (lrcc_debug_fail_allocs): the next
+// g_fail_allocs device allocations of the library fail as if cudaMalloc had.
+std::atomic<int> g_fail_allocs{0};
+bool inject_alloc_failure() {
+    int k = g_fail_allocs.load();
+    while (k > 0)
+        if (g_fail_allocs.compare_exchange_weak(k, k - 1)) return true;
+    return false;
+}
 
 std::mutex g_mu;
 std::atomic<int> g_timing{0};
@@ -236,6 +255,7 @@ lrcc_status ensure_ws(Ctx* c, size_t bytes) {
         c->ws_bytes = 0;
     }
     const size_t want = std::max(bytes, old + old / 4);
+    if (inject_alloc_failure()) return LRCC_ERR_NOMEM;
     if (cudaMalloc(&c->ws, want) != cudaSuccess) {
         cudaGetLastError();
         if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
@@ -261,7 +281,7 @@ lrcc_status ensure_io(Ctx* c, size_t bytes) {
         c->io = nullptr;
         c->io_bytes = 0;
     }
-    if (cudaMalloc(&c->io, bytes) != cudaSuccess) {
+    if (inject_alloc_failure() || cudaMalloc(&c->io, bytes) != cudaSuccess) {
         cudaGetLastError();
         c->io = nullptr;
         return LRCC_ERR_NOMEM;
@@ -380,6 +400,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
 
 lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    ApiRange range_("lr_rank");
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
     if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
@@ -392,6 +413,7 @@ lrcc_status lr_rank(const int32_t* succ, int64_t n, int32_t head, int32_t* rank,
 
 lrcc_status lr_rank_splitters(const int32_t* succ, int64_t n, int32_t head, const int32_t* spl, int64_t r,
                               int32_t* rank, void* stream) {
+    ApiRange range_("lr_rank_splitters");
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
     if (!succ || !rank || !spl || head < 0 || head >= n || r < 1 || r > n) return LRCC_ERR_ARG;
@@ -421,6 +443,7 @@ lrcc_status lr_rank_splitters(const int32_t* succ, int64_t n, int32_t head, cons
 }
 
 lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t head, int32_t* out, void* stream) {
+    ApiRange range_("lr_scan");
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
     if (!succ || !val || !out || head < 0 || head >= n) return LRCC_ERR_ARG;
@@ -432,6 +455,7 @@ lrcc_status lr_scan(const int32_t* succ, const int32_t* val, int64_t n, int32_t 
 }
 
 lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, int32_t* out, void* stream) {
+    ApiRange range_("lr_scan_forest");
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
     if (!succ || !val || !out) return LRCC_ERR_ARG;
@@ -453,6 +477,7 @@ lrcc_status lr_scan_forest(const int32_t* succ, const int32_t* val, int64_t n, i
 }
 
 lrcc_status lr_rank_host(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    ApiRange range_("lr_rank_host");
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
     if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
@@ -472,6 +497,7 @@ lrcc_status lr_rank_host(const int32_t* succ, int64_t n, int32_t head, int32_t* 
 }
 
 lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t* rank, void* stream) {
+    ApiRange range_("lr_rank_wyllie");
     if (n < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return LRCC_OK;
     if (!succ || !rank || head < 0 || head >= n) return LRCC_ERR_ARG;
@@ -497,6 +523,7 @@ lrcc_status lr_rank_wyllie(const int32_t* succ, int64_t n, int32_t head, int32_t
 
 lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label,
                      void* stream) {
+    ApiRange range_("cc_label");
     if (n < 0 || m < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return m == 0 ? LRCC_OK : LRCC_ERR_ARG;
     if (!label || (m > 0 && (!src || !dst))) return LRCC_ERR_ARG;
@@ -509,6 +536,7 @@ lrcc_status cc_label(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
 
 lrcc_status cc_label_host(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t* label,
                           void* stream) {
+    ApiRange range_("cc_label_host");
     if (n < 0 || m < 0 || n > 0x7FFFFFFELL) return LRCC_ERR_ARG;
     if (n == 0) return m == 0 ? LRCC_OK : LRCC_ERR_ARG;
     if (!label || (m > 0 && (!src || !dst))) return LRCC_ERR_ARG;
@@ -536,6 +564,7 @@ lrcc_status cc_label_host(const int32_t* src, const int32_t* dst, int64_t m, int
 
 lrcc_status lr_rank_batched_sized(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
                                   int64_t num_lists, int64_t total_nodes, int32_t* rank, void* stream) {
+    ApiRange range_("lr_rank_batched_sized");
     if (num_lists < 0 || total_nodes < 0) return LRCC_ERR_ARG;
     if (num_lists == 0) return LRCC_OK;
     if (!node_off || !heads || (total_nodes > 0 && (!succ || !rank))) return LRCC_ERR_ARG;
@@ -564,6 +593,7 @@ lrcc_status lr_rank_batched_sized(const int32_t* succ, const int64_t* node_off, 
 
 lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const int32_t* heads,
                             int64_t num_lists, int32_t* rank, void* stream) {
+    ApiRange range_("lr_rank_batched");
     if (num_lists < 0) return LRCC_ERR_ARG;
     if (num_lists == 0) return LRCC_OK;
     if (!node_off || !heads) return LRCC_ERR_ARG;
@@ -580,6 +610,7 @@ lrcc_status lr_rank_batched(const int32_t* succ, const int64_t* node_off, const 
 lrcc_status cc_label_batched_sized(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
                                    const int64_t* vert_off, int64_t num_graphs, int64_t total_edges,
                                    int32_t* label, void* stream) {
+    ApiRange range_("cc_label_batched_sized");
     if (num_graphs < 0 || total_edges < 0) return LRCC_ERR_ARG;
     if (num_graphs == 0) return LRCC_OK;
     if (!edge_off || !vert_off || !label || (total_edges > 0 && (!src || !dst))) return LRCC_ERR_ARG;
@@ -598,6 +629,7 @@ lrcc_status cc_label_batched_sized(const int32_t* src, const int32_t* dst, const
 
 lrcc_status cc_label_batched(const int32_t* src, const int32_t* dst, const int64_t* edge_off,
                              const int64_t* vert_off, int64_t num_graphs, int32_t* label, void* stream) {
+    ApiRange range_("cc_label_batched");
     if (num_graphs < 0) return LRCC_ERR_ARG;
     if (num_graphs == 0) return LRCC_OK;
     if (!edge_off || !vert_off) return LRCC_ERR_ARG;
@@ -620,6 +652,8 @@ lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m,
     std::lock_guard<std::mutex> lk(c->mu);
     return cc_gather_probe_run(c, src, dst, m, table, n, out);
 }
+
+int lrcc_debug_fail_allocs(int count) { return g_fail_allocs.exchange(count < 0 ? 0 : count); }
 
 lrcc_status lrcc_wait_check(int polls, void* stream) {
     if (polls < 1 || polls > (1 << 20)) return LRCC_ERR_ARG;

@@ -117,11 +117,17 @@ class Server:
         self.stop_flag = False
         self.t_first = None
         self.errors = 0
+        self.cancelled = 0
+        self.dead: BaseException | None = None   # why the scheduler stopped, if it failed
         self.thread = threading.Thread(target=self._loop, name="lrcc-serve", daemon=True)
         self.thread.start()
 
     # ------------------------------------------------------------ public
     def submit(self, job: Job) -> cf.Future:
+        """Queue a job; the future resolves to its result. A job whose future is
+        cancelled before it is launched is dropped."""
+        if self.dead is not None:
+            raise RuntimeError(f"serve: the scheduler stopped: {self.dead!r}")
         if job.device_bytes() > self.mem_budget or job.n > self.out_cap:
             raise ValueError("job larger than the server's memory budget or output buffer")
         job.future = cf.Future()
@@ -166,7 +172,8 @@ class Server:
         elems = sum(j.n + j.m for j in jobs)
         return {"jobs": len(jobs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "jobs_per_s": len(jobs) / span, "melems_per_s": elems / span / 1e6,
-                "errors": self.errors, "workspace_bytes": self.ws_bytes, "peak_device_bytes": self.peak}
+                "errors": self.errors, "cancelled": self.cancelled, "workspace_bytes": self.ws_bytes,
+                "peak_device_bytes": self.peak}
 
     # ---------------------------------------------------------- internals
     def _unit_ws(self, jobs: list) -> int:
@@ -185,6 +192,10 @@ class Server:
 
     def _take_unit(self, slot: int):
         """Pick the next launch unit for `slot` from the waiting jobs (lock held)."""
+        if any(j.future.cancelled() for j in self.pending):
+            kept = collections.deque(j for j in self.pending if not j.future.cancelled())
+            self.cancelled += len(self.pending) - len(kept)
+            self.pending = kept
         if not self.pending:
             return None
         first = self.pending[0]
@@ -313,6 +324,30 @@ class Server:
 
     def _loop(self) -> None:
         torch.cuda.set_device(self.device)
+        try:
+            self._run()
+        except BaseException as exc:   # a failed scheduler fails every job it holds, never hangs them
+            self._fail_all(exc)
+
+    def _fail_all(self, exc: BaseException) -> None:
+        with self.lock:
+            self.dead = exc
+            waiting = list(self.pending)
+            running = [j for u in self.inflight for j in u.jobs]
+            self.pending.clear()
+            self.inflight = []
+            self.errors += len(waiting) + len(running)
+        err = RuntimeError(f"serve: the scheduler stopped: {exc!r}")
+        for j in waiting:   # not started: a cancelled one stays cancelled
+            if j.future.set_running_or_notify_cancel():
+                j.t_done = time.perf_counter()
+                j.future.set_exception(err)
+        for j in running:
+            if not j.future.done():
+                j.t_done = time.perf_counter()
+                j.future.set_exception(err)
+
+    def _run(self) -> None:
         while True:
             # completions
             finished = [u for u in self.inflight if u.event.query()]
@@ -330,6 +365,13 @@ class Server:
                     if picked is None:
                         break
                     jobs, need = picked
+                    # a job cancelled since it was picked is dropped now; the others run
+                    live = [j for j in jobs if j.future.set_running_or_notify_cancel()]
+                    self.cancelled += len(jobs) - len(live)
+                    if not live:
+                        continue
+                    if len(live) != len(jobs):
+                        jobs, need = live, self._unit_ws(live)
                     self.busy[slot] = True
                     self.used += sum(j.device_bytes() for j in jobs)
                     self.peak = max(self.peak, self.used + self.ws_bytes)

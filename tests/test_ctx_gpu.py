@@ -60,3 +60,25 @@ def test_context_reports_device_errors_of_its_stream():
 def test_bad_device_is_an_argument_error():
     with pytest.raises(lrcc.LrccError):
         lrcc.Context(torch.cuda.device_count())
+
+
+def test_injected_allocation_failure_is_reported_and_recovers():
+    dev = torch.device("cuda", 0)
+    succ, head, perm = gen.list_random(1 << 20, 73, with_perm=True)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        sd = torch.from_numpy(succ).to(dev)
+        out = torch.empty_like(sd)
+    s.synchronize()
+    try:
+        assert lrcc.debug_fail_allocs(1) == 0
+        with pytest.raises(lrcc.LrccError) as e:
+            lrcc.lr_rank(sd, head, out=out, stream=s)      # a new stream: its workspace is allocated now
+        assert e.value.status == lrcc.ERR_NOMEM
+        assert lrcc.debug_fail_allocs(0) == 0              # the one injected failure was used
+        lrcc.lr_rank(sd, head, out=out, stream=s)
+        assert lrcc.last_status(s) == lrcc.OK
+        assert np.array_equal(out.cpu().numpy()[perm], np.arange((1 << 20) - 1, -1, -1, dtype=np.int32))
+    finally:
+        lrcc.debug_fail_allocs(0)
+        lrcc.release(s)

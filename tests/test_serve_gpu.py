@@ -115,6 +115,61 @@ def test_workspace_is_reserved_counted_and_freed_through_a_context():
     assert lrcc.workspace_bytes() == before
 
 
+def test_cancelled_jobs_are_dropped():
+    # a budget that holds one job at a time, so later jobs wait; the cancelled
+    # ones never run and the others still give their exact results
+    jobs = _make_jobs(16, 4, lo=15, hi=16)
+    srv = serve.Server(0, mem_budget=6 << 20, streams=1, small_cutoff=0)
+    try:
+        futs = [srv.submit_list(j[1], j[2]) if j[0] == "list" else srv.submit_graph(j[1], j[2], j[3]) for j in jobs]
+        dropped = [i for i in range(4, 16, 3) if futs[i].cancel()]
+        for i, (j, f) in enumerate(zip(jobs, futs)):
+            if i in dropped:
+                assert f.cancelled()
+            else:
+                assert np.array_equal(f.result(timeout=60), j[3] if j[0] == "list" else j[4])
+        srv.drain(60)
+        assert srv.stats()["cancelled"] == len(dropped)
+    finally:
+        srv.close()
+
+
+def test_failed_scheduler_fails_its_jobs_instead_of_hanging():
+    # a fault on the host inside the scheduler (injected by replacing its unit
+    # choice): every job it holds fails at once, and later submits are refused
+    srv = serve.Server(0, streams=2)
+    try:
+        def broken(slot):
+            raise RuntimeError("injected scheduler fault")
+        srv._take_unit = broken
+        succ, head = gen.list_random(10_000, 7)
+        f = srv.submit_list(torch.from_numpy(succ).pin_memory(), head)
+        with pytest.raises(RuntimeError, match="scheduler stopped"):
+            f.result(timeout=30)
+        with pytest.raises(RuntimeError, match="scheduler stopped"):
+            srv.submit_list(torch.from_numpy(succ).pin_memory(), head)
+    finally:
+        srv.close()
+
+
+def test_allocation_failure_fails_its_unit_only():
+    # the library's next workspace allocation fails (host-side injection): the job
+    # that needed it fails with ERR_NOMEM, and the server goes on with the next one
+    srv = serve.Server(0, streams=1, small_cutoff=0)
+    try:
+        succ, head = gen.list_random(1 << 20, 8)
+        lrcc.debug_fail_allocs(1)
+        f_bad = srv.submit_list(torch.from_numpy(succ).pin_memory(), head)
+        with pytest.raises(lrcc.LrccError) as e:
+            f_bad.result(timeout=60)
+        assert e.value.status == lrcc.ERR_NOMEM
+        f_ok = srv.submit_list(torch.from_numpy(succ).pin_memory(), head)
+        assert np.array_equal(f_ok.result(timeout=60), oracle.lr_rank(succ, head))
+    finally:
+        lrcc.debug_fail_allocs(0)
+        srv.close()
+
+
 def test_invalid_job_fails_only_its_unit():
     srv = serve.Server(0, streams=2, small_cutoff=1 << 10)
     try:

@@ -64,7 +64,7 @@ def _lr_candidates(log2n, quick):
     # full search the split mark / rank arrays as well
     level0 = ((1, 2) if log2n >= 22 else (1,)) + (() if quick else (3,))
     sp0 = (8, 32) if quick else (8, 16, 32, 64)
-    sp = (8,) if quick else (8, 16, 32)
+    sp = (8,) if quick else (4, 8, 16, 32)
     small = (16384,) if quick else (4096, 8192, 16384)
     chains = (1,) if quick else (1, 2)
     for l0, d0, d, sm, ch in itertools.product(level0, sp0, sp, small, chains):

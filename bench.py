@@ -302,6 +302,31 @@ def random_gather_peak(torch, dev, stream, log2n=28):
     return (1 << log2n) / (ms / 1e3) / 1e9
 
 
+def chase_peak(lrcc, torch, succ, stream, chain_logs=(19, 20, 21, 22, 23)):
+    """Dependent 4-byte reads of the bench's own successor array per second, in
+    G/s, from the library's chase probe (the first-level walk's load form, none
+    of its work), best over a few chain counts, each reading about n successors;
+    returns (rate, chains)."""
+    n = succ.numel()
+    best = (0.0, 0)
+    for lc in chain_logs:
+        chains = 1 << lc
+        steps = max(1, (n + chains - 1) // chains)
+        lrcc.chase_probe(succ, chains, steps, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(2):
+                lrcc.chase_probe(succ, chains, steps, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        lrcc.check(stream)
+        rate = chains * steps / (e0.elapsed_time(e1) / 2 / 1e3) / 1e9
+        if rate > best[0]:
+            best = (rate, chains)
+    return best
+
+
 def bench_lr_sweep(lrcc, torch, dev, stream, sizes=(16, 18, 20, 22, 24, 26, 28)):
     """List-ranking throughput against list size for the three first-level layouts
     (in-place 8-byte words, read-only walk with chunked records, split mark and
@@ -909,15 +934,21 @@ def main():
                 and args.workload == "large":
             traffic = NCU_WALK0["bytes_per_launch"]
         gather = random_gather_peak(torch, dev, stream)
+        chase, chase_chains = chase_peak(lrcc, torch, succ, stream)
         steps_per_s = n_lr / (per_launch_ms / 1e3) / 1e9
         roofline = {"kernel": "rs_walk0c (first-level sublist walk)" if level0 == 2 else "rs_walk (first level)",
                     "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": traffic, "ms_per_launch": per_launch_ms,
                     "algorithmic_bytes": per_elem,
                     "random_access": {
-                        "achieved_g_steps_per_s": steps_per_s, "peak_g_per_s": gather,
-                        "peak_kind": "measured here: torch index_select of 2^28 random 4-byte elements",
-                        "frac": steps_per_s / gather,
+                        "achieved_g_steps_per_s": steps_per_s, "peak_g_per_s": chase,
+                        "peak_kind": f"measured here: lrcc_chase_probe, {chase_chains} chains of dependent "
+                                     "4-byte reads over the same successor array (the walk's load form, none of "
+                                     "its work), best of 2^19 .. 2^23 chains (more than fit at once run in waves)",
+                        "frac": steps_per_s / chase,
+                        "independent_gathers_g_per_s": gather,
+                        "independent_gathers_kind": "torch index_select of 2^28 random 4-byte elements",
+                        "frac_of_independent_gathers": steps_per_s / gather,
                         "note": "each walk step is one dependent random read of succ; HBM row activations, "
                                 "not bytes, bound random access"}}
         # the other kernels of the step, each against the bound that applies to it

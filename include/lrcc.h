@@ -263,6 +263,20 @@ lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m,
                               int64_t* out, void* stream);
 
 /*
+ * Measurement aid: the access pattern of the first-level sublist walk (Sec. 3.2,
+ * RS3) without its work. `chains` chains of dependent reads over succ (int32[n],
+ * device): chain c starts at element floor(c * n / chains) and reads `steps`
+ * successors one after the other, with the walk's load form; a chain that
+ * reaches a tail (-1 or a self-loop) or an id outside [0, n) continues from a
+ * hashed element, which costs no read. The wrapped sum of the elements reached
+ * goes to *out (a device int64), so no load is dropped. chains in [1, 2^31],
+ * steps >= 0. Asynchronous on `stream`; allocates nothing beyond the stream's
+ * status word.
+ */
+lrcc_status lrcc_chase_probe(const int32_t* succ, int64_t n, int64_t chains, int64_t steps, int64_t* out,
+                             void* stream);
+
+/*
  * Fault injection on the host, for testing a caller's out-of-memory handling:
  * the next `count` device allocations the library makes (workspaces, host-call
  * staging) fail as if cudaMalloc had, and the calls that needed them return

@@ -37,7 +37,7 @@ SYMBOLS = ("lrcc_status_str", "lrcc_version", "lr_rank", "lr_rank_wyllie", "lr_r
            "lrcc_workspace_query", "lrcc_set_timing", "lrcc_phase_count", "lrcc_phase_name",
            "lrcc_phase_times", "lrcc_set_l2_fetch_granularity", "lrcc_get_l2_fetch_granularity",
            "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_bytes", "lrcc_ctx_last_status", "lrcc_ctx_destroy",
-           "lrcc_gather_probe", "lr_rank_splitters", "lrcc_debug_fail_allocs")
+           "lrcc_gather_probe", "lrcc_chase_probe", "lr_rank_splitters", "lrcc_debug_fail_allocs")
 
 
 class LrccError(RuntimeError):
@@ -114,6 +114,7 @@ def load() -> ctypes.CDLL:
         lib.lrcc_ctx_destroy.argtypes = [p]
         lib.lrcc_ctx_destroy.restype = None
         lib.lrcc_gather_probe.argtypes = [p, p, i64, p, i64, p, p]
+        lib.lrcc_chase_probe.argtypes = [p, i64, i64, i64, p, p]
         lib.lr_rank_splitters.argtypes = [p, i64, i32, p, i64, p, p]
         lib.lrcc_debug_fail_allocs.argtypes = [i]
         lib.lrcc_debug_fail_allocs.restype = i
@@ -125,7 +126,7 @@ def load() -> ctypes.CDLL:
                   "lrcc_last_status", "lrcc_last_stats", "lrcc_wait_check", "lrcc_set_plan", "lrcc_get_plan", "lrcc_reset_plans",
                   "lrcc_release", "lrcc_set_timing", "lrcc_phase_times", "lrcc_set_l2_fetch_granularity",
                   "lrcc_ctx_create", "lrcc_ctx_reserve", "lrcc_ctx_last_status", "lrcc_gather_probe",
-                  "lr_rank_splitters"):
+                  "lrcc_chase_probe", "lr_rank_splitters"):
             getattr(lib, f).restype = i
         _lib = lib
         return lib
@@ -405,6 +406,17 @@ def gather_probe(src: torch.Tensor, dst: torch.Tensor, table: torch.Tensor, stre
     out = torch.zeros(1, dtype=torch.int64, device=table.device)
     _call(load().lrcc_gather_probe(src.data_ptr(), dst.data_ptr(), src.numel(), table.data_ptr(), table.numel(),
                                    out.data_ptr(), _stream(stream)), "lrcc_gather_probe")
+    return out
+
+
+def chase_probe(succ: torch.Tensor, chains: int, steps: int, stream=None) -> torch.Tensor:
+    """`chains` chains of `steps` dependent reads of succ each, with the first-level
+    walk's load form and none of its work (lrcc_chase_probe): a ceiling for the
+    walk. Returns the device int64 sum of the elements reached."""
+    succ = _dev_i32(succ, "succ")
+    out = torch.zeros(1, dtype=torch.int64, device=succ.device)
+    _call(load().lrcc_chase_probe(succ.data_ptr(), succ.numel(), int(chains), int(steps), out.data_ptr(),
+                                  _stream(stream)), "lrcc_chase_probe")
     return out
 
 

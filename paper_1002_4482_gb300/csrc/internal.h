@@ -158,6 +158,9 @@ cudaError_t wait_check_enqueue(DevCtl* ctl, int polls, cudaStream_t s);
 lrcc_status lr_enqueue_wyllie(Ctx* c, cudaStream_t s, const int32_t* succ, int64_t n, int32_t head,
                               int32_t* rank, const Plan& p);
 size_t lr_wyllie_ws(int64_t n, const Plan& p);
+// Dependent reads of succ without the walk's work (the walk's ceiling).
+lrcc_status rs_chase_probe_run(Ctx* c, const int32_t* succ, int64_t n, int64_t chains, int64_t steps,
+                               int64_t* out);
 
 // --- connected components (cc.cu)
 lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,

@@ -323,6 +323,45 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+// Ceiling of the first-level walk's access pattern: dependent 4-byte reads of
+// succ, with the walk's load form and none of its bookkeeping (no chunk
+// writes, no splitter test). Chain c of `chains` starts at element
+// floor(c * n / chains) and takes `steps` steps; a chain that reaches a tail
+// (or an id outside [0, n)) continues from a hashed element, which costs no
+// read. Each thread advances PROBE_K chains together, as the walk does; the
+// wrapped sum of the elements reached goes to *out, so no load is dropped.
+constexpr int PROBE_K = 4;
+__global__ void __launch_bounds__(BLOCK)
+    rs_chase_probe(const int32_t* __restrict__ succ, int64_t n, int64_t chains, int64_t steps,
+                   unsigned long long* out) {
+    const int64_t c0 = ((int64_t)blockIdx.x * BLOCK + threadIdx.x) * PROBE_K;
+    int64_t cur[PROBE_K];
+    bool live[PROBE_K];
+#pragma unroll
+    for (int q = 0; q < PROBE_K; ++q) {
+        live[q] = c0 + q < chains;
+        cur[q] = live[q] ? (c0 + q) * n / chains : 0;   // c < 2^31 and n <= 2^31: no overflow
+    }
+    unsigned long long acc = 0;
+    for (int64_t k = 0; k < steps; ++k) {
+        int32_t nx[PROBE_K];
+#pragma unroll
+        for (int q = 0; q < PROBE_K; ++q) nx[q] = live[q] ? __ldcs(succ + cur[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < PROBE_K; ++q) {
+            if (!live[q]) continue;
+            int64_t x = nx[q];
+            if (x < 0 || x >= n || x == cur[q])
+                x = (int64_t)(((uint64_t)mix32((uint32_t)cur[q] ^ (uint32_t)k * 0x9E3779B9u) * (uint64_t)n) >> 32);
+            acc += (unsigned long long)x;
+            cur[q] = x;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 // ------------------------------------------------ level 0, read-only walk
 //
 // Random HBM accesses are limited by row activations, not bytes: a random
@@ -600,9 +639,14 @@ __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int 
 // each bucket. Radix-partition style, in rounds of SC_CHUNKS chunks: the
 // round's chunk ids and headers arrive in shared memory by bulk copy (SC_BUF
 // buffers: the next rounds in flight while this one is processed), the
-// round's elements are ranked by bucket with shared atomics, their indices
-// laid out sorted by bucket in a tile, and every bucket's run is written
-// with coalesced stores at the block's next offset for that bucket. Blocks
+// round's elements are ranked by bucket with shared atomics, their
+// (element, rank) pairs laid out sorted by bucket in a tile, and every
+// bucket's run is written with coalesced stores at the block's next offset
+// for that bucket. The phases of a round are separated by block barriers and
+// the kernel is bound by their latency, not by shared-memory bandwidth: at
+// 2^28 elements the pair tile (2 blocks per SM) takes 1.38 ms, a tile of
+// 16-bit slot indices with 4 blocks per SM 1.44 ms, and rounds of 3 chunks
+// per thread 1.47 ms. Blocks
 // are persistent and take work units u = blockIdx.x, + gridDim.x, ...: the
 // NSEG segments of every walk block's region, then the segments of the shared
 // overflow pool (each unit's per-bucket counts come from the walk).
@@ -617,9 +661,8 @@ constexpr int SC_WAIT_LIMIT = 1 << 18;
 struct ScatterSmem {
     int32_t ids[SC_BUF][SC_ITEMS];      // chunk ids of the round in each buffer
     uint64_t meta[SC_BUF][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
-    int32_t top[SC_CHUNKS];        // rank of the first element of each chunk
-    uint16_t tile[SC_ITEMS];       // slot indices sorted by bucket
-    int cnt[2][NBK];               // elements per bucket in the round (alternating)
+    uint64_t tile[SC_ITEMS];       // the round's (element, rank) pairs sorted by bucket
+    int cnt[NBK];                  // elements per bucket in the round
     int base[NBK];                 // next free pair of each bucket for this region
     int delta[NBK];                // pair position minus tile slot, per bucket, in the round
     int tstart[NBK];               // start of each bucket's run in the tile
@@ -640,13 +683,12 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int32_t (&id)[CIDS]
     id[4] = hi.x; id[5] = hi.y; id[6] = hi.z; id[7] = hi.w;
 }
 
-__global__ void __launch_bounds__(BLOCK, 4)
+__global__ void __launch_bounds__(BLOCK, 2)
     rs_scatter(Chunks C, int G, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n,
                DevCtl* ctl) {
     extern __shared__ __align__(128) unsigned char sc_raw[];
     ScatterSmem& s = *reinterpret_cast<ScatterSmem*>(sc_raw);
     static_assert(NBK == BLOCK, "one thread per bucket");
-    static_assert(SC_ITEMS <= 65536, "tile holds 16-bit slot indices");
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     // block-wide exclusive scan of one value per thread (uses s.warp; two syncs)
     auto block_scan = [&](int v, int* total) {
@@ -675,7 +717,7 @@ __global__ void __launch_bounds__(BLOCK, 4)
         bstart = block_scan(C.totals[t], &all);
         if (blockIdx.x == 0 && t == 0) ctl->pairs = all;
     }
-    s.cnt[0][t] = s.cnt[1][t] = 0;
+    s.cnt[t] = 0;
     if (t == 0) {
         for (int b = 0; b < SC_BUF; ++b) mbar_init(&s.bar[b], 1);
         fence_proxy_async_smem();   // the initialised barriers are visible to the bulk copies
@@ -684,7 +726,6 @@ __global__ void __launch_bounds__(BLOCK, 4)
     const uint64_t pol = policy_evict_first();
     uint32_t phase = 0;             // bit b: parity of the next completion of buffer b's barrier
     uint32_t in_flight = 0;         // bit b: a copy into buffer b is not yet waited for (thread 0)
-    int par = 0;                    // which cnt array the next round counts in
     bool failed = false;
 
     // issue the bulk copy of round k of region g (chunks own0 + k*SC_CHUNKS ..) into buffer b
@@ -703,10 +744,8 @@ __global__ void __launch_bounds__(BLOCK, 4)
     // one round over buffer b, whose chunks [0, cnt) are valid (a chunk whose
     // first id is -1 is empty)
     auto process = [&](int b, int cnt) {
-        int* cntp = s.cnt[par];
-        // the owners' suffix ranks (L2 gathers) are issued first and stored to shared
-        // memory only after the tile is built, so their latency overlaps the counting,
-        // the scan and the tile
+        // the owners' suffix ranks (L2 gathers) are issued first, so their latency
+        // overlaps the counting and the scan
         int32_t top[SC_U];
 #pragma unroll
         for (int u = 0; u < SC_U; ++u) {
@@ -714,19 +753,21 @@ __global__ void __launch_bounds__(BLOCK, 4)
             const uint64_t mt = s.meta[b][c];
             top[u] = (c < cnt && s.ids[b][c * CIDS] >= 0) ? __ldg(S1 + lo32(mt)) - 1 - (int32_t)hi32(mt) : 0;
         }
+        int32_t id[SC_U][CIDS];
         int loc[SC_U][CIDS];
 #pragma unroll
         for (int u = 0; u < SC_U; ++u) {
             const int c = u * BLOCK + t;
-            int32_t id[CIDS];
-            load_chunk(&s.ids[b][c * CIDS], id);
+            load_chunk(&s.ids[b][c * CIDS], id[u]);
 #pragma unroll
-            for (int q = 0; q < CIDS; ++q)
-                loc[u][q] = (c < cnt && id[q] >= 0) ? atomicAdd(&cntp[id[q] >> C.shift], 1) : 0;
+            for (int q = 0; q < CIDS; ++q) {
+                if (c >= cnt) id[u][q] = -1;
+                loc[u][q] = id[u][q] >= 0 ? atomicAdd(&s.cnt[id[u][q] >> C.shift], 1) : 0;
+            }
         }
         __syncthreads();
-        const int h = s.cnt[par][t];
-        s.cnt[par ^ 1][t] = 0;      // counts of the next round
+        const int h = s.cnt[t];
+        s.cnt[t] = 0;               // counts of the next round
         int items = 0;
         const int ts = block_scan(h, &items);
         s.tstart[t] = ts;
@@ -734,26 +775,20 @@ __global__ void __launch_bounds__(BLOCK, 4)
         s.base[t] += h;
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < SC_U; ++u) {
-            const int c = u * BLOCK + t;
-            int32_t id[CIDS];
-            load_chunk(&s.ids[b][c * CIDS], id);
+        for (int u = 0; u < SC_U; ++u)
 #pragma unroll
             for (int q = 0; q < CIDS; ++q)
-                if (c < cnt && id[q] >= 0) s.tile[s.tstart[id[q] >> C.shift] + loc[u][q]] = (uint16_t)(c * CIDS + q);
-        }
-#pragma unroll
-        for (int u = 0; u < SC_U; ++u) s.top[u * BLOCK + t] = top[u];
+                if (id[u][q] >= 0)
+                    s.tile[s.tstart[id[u][q] >> C.shift] + loc[u][q]] =
+                        pack((uint32_t)id[u][q], (uint32_t)(top[u] - q));
         __syncthreads();
         for (int i = t; i < items; i += BLOCK) {
-            const int x = s.tile[i];
-            const int32_t id = s.ids[b][x];
-            const int64_t pos = (int64_t)s.delta[id >> C.shift] + i;
-            if (pos < n) pairs[pos] = pack((uint32_t)id, (uint32_t)(s.top[x >> 3] - (x & 7)));
+            const uint64_t pr = s.tile[i];
+            const int64_t pos = (int64_t)s.delta[lo32(pr) >> C.shift] + i;
+            if (pos < n) pairs[pos] = pr;
         }
         fence_proxy_async_smem();   // the buffer's reads come before the next bulk copy into it
         __syncthreads();
-        par ^= 1;
     };
 
     const int64_t no_all = min((int64_t)ctl->ovf_next, C.ovf_cap);
@@ -1580,6 +1615,16 @@ int stream_grid(Ctx* c, int64_t groups, const void* kernel) {
 }  // namespace
 
 // --------------------------------------------------------------- planning
+
+lrcc_status rs_chase_probe_run(Ctx* c, const int32_t* succ, int64_t n, int64_t chains, int64_t steps,
+                               int64_t* out) {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), c->stream);
+    const int64_t threads = (chains + PROBE_K - 1) / PROBE_K;
+    const int64_t g = (threads + BLOCK - 1) / BLOCK;
+    rs_chase_probe<<<(unsigned)g, BLOCK, 0, c->stream>>>(succ, n, chains, steps,
+                                                         reinterpret_cast<unsigned long long*>(out));
+    return cuda_status(cudaGetLastError());
+}
 
 int rs_walk_grid(Ctx* c, const Plan& p) {
     const void* k = p.rs_chains >= 4 ? (const void*)rs_walk0c<4>

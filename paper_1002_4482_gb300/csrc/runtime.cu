@@ -655,6 +655,16 @@ lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m,
     return cc_gather_probe_run(c, src, dst, m, table, n, out);
 }
 
+lrcc_status lrcc_chase_probe(const int32_t* succ, int64_t n, int64_t chains, int64_t steps, int64_t* out,
+                             void* stream) {
+    if (n < 1 || chains < 1 || chains > (int64_t(1) << 31) || steps < 0 || !succ || !out) return LRCC_ERR_ARG;
+    Ctx* c = nullptr;
+    lrcc_status st = ctx_for(stream, &c);
+    if (st != LRCC_OK) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return rs_chase_probe_run(c, succ, n, chains, steps, out);
+}
+
 int lrcc_debug_fail_allocs(int count) { return g_fail_allocs.exchange(count < 0 ? 0 : count); }
 
 lrcc_status lrcc_wait_check(int polls, void* stream) {

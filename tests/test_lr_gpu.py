@@ -304,3 +304,28 @@ def test_given_splitters_errors():
         assert lrcc.last_status() == lrcc.ERR_INVALID_INPUT
     with pytest.raises(lrcc.LrccError):
         lrcc.lr_rank_splitters(t, head, torch.zeros(0, dtype=torch.int32, device=DEV))
+
+
+@pytest.mark.parametrize("n,chains,steps", [(1, 1, 5), (100_003, 1000, 37), (70_001, 4099, 0), (1 << 16, 1 << 14, 300)])
+def test_chase_probe_follows_successors(n, chains, steps):
+    # on the cyclic list i -> i + 1 (mod n) chain c starts at floor(c n / chains) and
+    # reaches start + 1, ..., start + steps (mod n); n = 1 is a self-loop, so every
+    # step of its chains restarts at element 0
+    succ = ((np.arange(n, dtype=np.int64) + 1) % n).astype(np.int32)
+    got = lrcc.chase_probe(torch.from_numpy(succ).to(DEV), chains, steps)
+    lrcc.check()
+    start = np.arange(chains, dtype=np.int64) * n // chains
+    k = np.arange(1, steps + 1, dtype=np.int64)
+    want = int(((start[:, None] + k[None, :]) % n).sum()) if n > 1 else 0
+    assert int(got.item()) == want
+
+
+def test_chase_probe_on_a_list_with_a_tail_and_bad_arguments():
+    succ, head = gen.list_random(50_000, 9)
+    s = torch.from_numpy(succ).to(DEV)
+    got = lrcc.chase_probe(s, 2048, 100)
+    lrcc.check()
+    assert 0 < int(got.item()) <= 2048 * 100 * 49_999
+    for chains, steps in ((0, 10), (-1, 10), (10, -1), ((1 << 31) + 1, 1)):
+        with pytest.raises(lrcc.LrccError):
+            lrcc.chase_probe(s, chains, steps)

@@ -42,10 +42,10 @@ LR_METHOD_NOTE = {
 }
 
 # ncu DRAM bytes of one first-level walk launch (rs_walk0c) at n = 2^28, random
-# layout: dram__bytes_read.sum + dram__bytes_write.sum of a capture at n = 2^26
-# (7.575 GB + 0.425 GB; ncu of `bench.py --case lr 26 readonly`) scaled by the 4x elements,
-# and the hash of the walk's source it was taken from. Reported only while that source is unchanged.
-NCU_WALK0 = {"walk_sha1": "c03e14e73a8dee1b2e57b18147ea99029730c040", "bytes_per_launch": 4 * (7.574699264e9 + 0.424686848e9)}
+# layout: dram__bytes_read.sum + dram__bytes_write.sum of a one-pass capture of
+# `bench.py --case lr 28 readonly` (31.873 GB + 1.716 GB), and the hash of the walk's
+# source it was taken from. Reported only while that source is unchanged.
+NCU_WALK0 = {"walk_sha1": "be5c2d895b7500d72fc0f7f0895cd3ae9fd53d7d", "bytes_per_launch": 31873228288 + 1715904768}
 
 
 def log(*a):

@@ -269,9 +269,9 @@ lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m,
  * successors one after the other, with the walk's load form; a chain that
  * reaches a tail (-1 or a self-loop) or an id outside [0, n) continues from a
  * hashed element, which costs no read. The wrapped sum of the elements reached
- * goes to *out (a device int64), so no load is dropped. chains in [1, 2^31],
- * steps >= 0. Asynchronous on `stream`; allocates nothing beyond the stream's
- * status word.
+ * goes to *out (a device int64), so no load is dropped. n in [1, 2^31 - 1],
+ * chains in [1, 2^31], steps >= 0 (LRCC_ERR_ARG otherwise). Asynchronous on
+ * `stream`; allocates nothing beyond the stream's status word.
  */
 lrcc_status lrcc_chase_probe(const int32_t* succ, int64_t n, int64_t chains, int64_t steps, int64_t* out,
                              void* stream);

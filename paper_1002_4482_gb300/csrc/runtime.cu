@@ -657,7 +657,8 @@ lrcc_status lrcc_gather_probe(const int32_t* src, const int32_t* dst, int64_t m,
 
 lrcc_status lrcc_chase_probe(const int32_t* succ, int64_t n, int64_t chains, int64_t steps, int64_t* out,
                              void* stream) {
-    if (n < 1 || chains < 1 || chains > (int64_t(1) << 31) || steps < 0 || !succ || !out) return LRCC_ERR_ARG;
+    if (n < 1 || n > INT32_MAX || chains < 1 || chains > (int64_t(1) << 31) || steps < 0 || !succ || !out)
+        return LRCC_ERR_ARG;
     Ctx* c = nullptr;
     lrcc_status st = ctx_for(stream, &c);
     if (st != LRCC_OK) return st;

@@ -86,6 +86,18 @@ def test_host_side_argument_errors_need_no_gpu(lib):
     assert L.cc_label(None, None, 0, 5, None, None) == lrcc.ERR_ARG
     assert L.lr_rank_batched(None, None, None, 0, None, None) == lrcc.OK
     assert L.cc_label_batched(None, None, None, None, -1, None, None) == lrcc.ERR_ARG
+    # measurement aids: sizes and pointers checked before the stream's state is touched
+    p16 = ctypes.c_void_p(16)
+    assert L.lrcc_chase_probe(p16, 0, 1, 1, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_chase_probe(p16, 1 << 31, 1, 1, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_chase_probe(p16, 10, 0, 1, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_chase_probe(p16, 10, (1 << 31) + 1, 1, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_chase_probe(p16, 10, 4, -1, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_chase_probe(None, 10, 4, 1, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_chase_probe(p16, 10, 4, 1, None, None) == lrcc.ERR_ARG
+    assert L.lrcc_gather_probe(p16, p16, -1, p16, 10, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_gather_probe(p16, p16, 4, p16, 0, p16, None) == lrcc.ERR_ARG
+    assert L.lrcc_gather_probe(None, p16, 4, p16, 10, p16, None) == lrcc.ERR_ARG
 
 
 def test_plan_table_roundtrip(lib):

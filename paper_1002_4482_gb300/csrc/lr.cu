@@ -684,21 +684,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int 
 
 // Chunks of walk block g -> (element, rank) pairs at block g's offsets of
 // each bucket. Radix-partition style, in rounds of SC_CHUNKS chunks: the
-// round's chunk ids and headers arrive in shared memory by bulk copy (SC_BUF
-// buffers: the next rounds in flight while this one is processed), the
+// round's chunk ids and headers arrive in shared memory by bulk copy, the
 // round's elements are ranked by bucket with shared atomics, their
 // (element, rank) pairs laid out sorted by bucket in a tile, and every
 // bucket's run is written with coalesced stores at the block's next offset
 // for that bucket. The phases of a round are separated by block barriers and
-// the kernel is bound by their latency, not by shared-memory bandwidth: at
-// 2^28 elements the pair tile (2 blocks per SM) takes 1.38 ms, a tile of
-// 16-bit slot indices with 4 blocks per SM 1.44 ms, and rounds of 3 chunks
-// per thread 1.47 ms. Blocks
+// the kernel is bound by their latency, not by shared-memory bandwidth, so
+// blocks per SM count most: at 2^28 elements a 16-bit slot-index tile with 4
+// blocks per SM took 1.44 ms, the pair tile with two staging buffers (2 blocks
+// per SM) 1.38 ms, rounds of 3 chunks per thread 1.47 ms, and the pair tile
+// with one staging buffer (3 blocks per SM) 1.22 ms. Blocks
 // are persistent and take work units u = blockIdx.x, + gridDim.x, ...: the
 // NSEG segments of every walk block's region, then the segments of the shared
 // overflow pool (each unit's per-bucket counts come from the walk).
 constexpr int SC_U = 2;                         // chunks per thread and round
-constexpr int SC_BUF = 2;                       // rounds staged in shared memory (in flight + current)
+// One staging buffer: a round's ids and headers move into registers in its
+// first phase, and the next round's bulk copy lands in the same buffer while
+// this round is scanned and written out (0.35 against 0.40 ms at 2^26).
+constexpr int SC_BUF = 1;
 constexpr int SC_CHUNKS = SC_U * BLOCK;         // chunks per round
 constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
 // Polls of a bulk-copy barrier before giving up. A poll that finds the phase
@@ -710,7 +713,6 @@ struct ScatterSmem {
     uint64_t meta[SC_BUF][SC_CHUNKS];   // chunk headers (k0 << 32 | owner)
     uint64_t tile[SC_ITEMS];       // the round's (element, rank) pairs sorted by bucket
     int cnt[NBK];                  // elements per bucket in the round
-    int base[NBK];                 // next free pair of each bucket for this region
     int delta[NBK];                // pair position minus tile slot, per bucket, in the round
     int tstart[NBK];               // start of each bucket's run in the tile
     int warp[BLOCK / 32];
@@ -730,7 +732,7 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int32_t (&id)[CIDS]
     id[4] = hi.x; id[5] = hi.y; id[6] = hi.z; id[7] = hi.w;
 }
 
-__global__ void __launch_bounds__(BLOCK, 2)
+__global__ void __launch_bounds__(BLOCK, 3)
     rs_scatter(Chunks C, int G, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n,
                DevCtl* ctl) {
     extern __shared__ __align__(128) unsigned char sc_raw[];
@@ -774,6 +776,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
     uint32_t phase = 0;             // bit b: parity of the next completion of buffer b's barrier
     uint32_t in_flight = 0;         // bit b: a copy into buffer b is not yet waited for (thread 0)
     bool failed = false;
+    int my_base = 0;                // next free pair of bucket t (this thread's) in the current unit
 
     // issue the bulk copy of round k of region g (chunks own0 + k*SC_CHUNKS ..) into buffer b
     auto issue = [&](int64_t first, int nf, int k, int b) {
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
 
     // one round over buffer b, whose chunks [0, cnt) are valid (a chunk whose
     // first id is -1 is empty)
-    auto process = [&](int b, int cnt) {
+    auto process = [&](int b, int cnt, int64_t uc0, int unf, int knext) {
         // the owners' suffix ranks (L2 gathers) are issued first, so their latency
         // overlaps the counting and the scan
         int32_t top[SC_U];
@@ -812,14 +815,18 @@ __global__ void __launch_bounds__(BLOCK, 2)
                 loc[u][q] = id[u][q] >= 0 ? atomicAdd(&s.cnt[id[u][q] >> C.shift], 1) : 0;
             }
         }
+        fence_proxy_async_smem();   // this thread's reads of the buffer come before the next copy into it
         __syncthreads();
+        // the round's ids and headers now sit in registers: the next round's copy goes
+        // into the same buffer while this one is scanned and written out
+        if (t == 0 && knext >= 0) issue(uc0, unf, knext, b);
         const int h = s.cnt[t];
         s.cnt[t] = 0;               // counts of the next round
         int items = 0;
         const int ts = block_scan(h, &items);
         s.tstart[t] = ts;
-        s.delta[t] = s.base[t] - ts;   // pair position of tile slot i of bucket t: delta[t] + i
-        s.base[t] += h;
+        s.delta[t] = my_base - ts;     // pair position of tile slot i of bucket t: delta[t] + i
+        my_base += h;
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < SC_U; ++u)
@@ -834,8 +841,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
             const int64_t pos = (int64_t)s.delta[lo32(pr) >> C.shift] + i;
             if (pos < n) pairs[pos] = pr;
         }
-        fence_proxy_async_smem();   // the buffer's reads come before the next bulk copy into it
-        __syncthreads();
+        __syncthreads();            // the next round rebuilds the tile
     };
 
     const int64_t no_all = min((int64_t)ctl->ovf_next, C.ovf_cap);
@@ -855,7 +861,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
             c0 = C.ovf_base + v0;
         }
         if (nf == 0) continue;
-        s.base[t] = bstart + C.counts[(int64_t)t * C.units + unit];
+        my_base = bstart + C.counts[(int64_t)t * C.units + unit];
         const int nr = (nf + SC_CHUNKS - 1) / SC_CHUNKS;
         if (t == 0)
             for (int k = 0; k < SC_BUF && k < nr; ++k) issue(c0, nf, k, k);
@@ -871,8 +877,7 @@ __global__ void __launch_bounds__(BLOCK, 2)
                 failed = true;
                 break;
             }
-            process(b, min(SC_CHUNKS, nf - k * SC_CHUNKS));
-            if (t == 0 && k + SC_BUF < nr) issue(c0, nf, k + SC_BUF, b);
+            process(b, min(SC_CHUNKS, nf - k * SC_CHUNKS), c0, nf, k + 1 < nr ? k + 1 : -1);
         }
     }
     if (failed) {

@@ -91,6 +91,16 @@ __device__ __forceinline__ int32_t ld_hint(const int32_t* p, uint64_t pol) {
     asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+// Read-only path with an L2 eviction-priority hint.
+__device__ __forceinline__ int32_t ld_nc_hint(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+// 8-byte store with an L2 eviction-priority hint.
+__device__ __forceinline__ void st_hint_u64(uint64_t* p, uint64_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(p), "l"(v), "l"(pol) : "memory");
+}
 __device__ __forceinline__ int32_t ld_cg_hint(const int32_t* p, uint64_t pol) {
     int32_t v;
     asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));

@@ -697,11 +697,27 @@ __global__ void __launch_bounds__(SCAN_THREADS) rs_scan_counts(int* counts, int 
 // are persistent and take work units u = blockIdx.x, + gridDim.x, ...: the
 // NSEG segments of every walk block's region, then the segments of the shared
 // overflow pool (each unit's per-bucket counts come from the walk).
-constexpr int SC_U = 2;                         // chunks per thread and round
+// Compile-time shape of a round: chunks per thread (SC_U), staging buffers
+// (SC_BUF) and the blocks per SM the launch bounds ask for. Rounds of one chunk
+// per thread with two or three buffers and 4-6 blocks per SM took 1.54-1.78 ms
+// at 2^28 against 1.21 ms for the default: a round's fixed cost (barriers, the
+// scan, the owners' gathers) is paid per round, so fewer, larger rounds win.
+#ifndef LRCC_SC_U
+#define LRCC_SC_U 2
+#endif
+#ifndef LRCC_SC_BUF
+#define LRCC_SC_BUF 1
+#endif
+#ifndef LRCC_SC_MINB
+#define LRCC_SC_MINB 3
+#endif
+
+constexpr int SC_U = LRCC_SC_U;                 // chunks per thread and round
 // One staging buffer: a round's ids and headers move into registers in its
 // first phase, and the next round's bulk copy lands in the same buffer while
-// this round is scanned and written out (0.35 against 0.40 ms at 2^26).
-constexpr int SC_BUF = 1;
+// this round is scanned and written out (0.35 against 0.40 ms at 2^26). With
+// more buffers, the copy issued after round k's first phase is round k + SC_BUF.
+constexpr int SC_BUF = LRCC_SC_BUF;
 constexpr int SC_CHUNKS = SC_U * BLOCK;         // chunks per round
 constexpr int SC_ITEMS = SC_CHUNKS * CIDS;      // element slots per round
 // Polls of a bulk-copy barrier before giving up. A poll that finds the phase
@@ -732,14 +748,16 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int32_t (&id)[CIDS]
     id[4] = hi.x; id[5] = hi.y; id[6] = hi.z; id[7] = hi.w;
 }
 
-__global__ void __launch_bounds__(BLOCK, 3)
+__global__ void __launch_bounds__(BLOCK, LRCC_SC_MINB)
     rs_scatter(Chunks C, int G, const int32_t* __restrict__ S1, uint64_t* __restrict__ pairs, int64_t n,
                DevCtl* ctl) {
     extern __shared__ __align__(128) unsigned char sc_raw[];
     ScatterSmem& s = *reinterpret_cast<ScatterSmem*>(sc_raw);
     static_assert(NBK == BLOCK, "one thread per bucket");
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    // block-wide exclusive scan of one value per thread (uses s.warp; two syncs)
+    // block-wide exclusive scan of one value per thread (uses s.warp; one sync).
+    // Every caller passes another block barrier before the next scan rewrites
+    // s.warp, so the scan needs no barrier after reading it.
     auto block_scan = [&](int v, int* total) {
         int incl = v;
 #pragma unroll
@@ -756,7 +774,6 @@ __global__ void __launch_bounds__(BLOCK, 3)
             off += w < wid ? x : 0;
             all += x;
         }
-        __syncthreads();
         *total = all;
         return off + incl - v;
     };
@@ -772,7 +789,11 @@ __global__ void __launch_bounds__(BLOCK, 3)
         fence_proxy_async_smem();   // the initialised barriers are visible to the bulk copies
     }
     __syncthreads();
+    // L2 hints: the chunks are read and the pairs written once (evict first),
+    // while the owners' suffix ranks S1 (4 bytes per splitter) are gathered
+    // once per chunk and should stay (evict last): 1.17 against 1.20 ms at 2^28
     const uint64_t pol = policy_evict_first();
+    const uint64_t keep = policy_evict_last();
     uint32_t phase = 0;             // bit b: parity of the next completion of buffer b's barrier
     uint32_t in_flight = 0;         // bit b: a copy into buffer b is not yet waited for (thread 0)
     bool failed = false;
@@ -801,7 +822,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
         for (int u = 0; u < SC_U; ++u) {
             const int c = u * BLOCK + t;
             const uint64_t mt = s.meta[b][c];
-            top[u] = (c < cnt && s.ids[b][c * CIDS] >= 0) ? __ldg(S1 + lo32(mt)) - 1 - (int32_t)hi32(mt) : 0;
+            top[u] = (c < cnt && s.ids[b][c * CIDS] >= 0) ? ld_nc_hint(S1 + lo32(mt), keep) - 1 - (int32_t)hi32(mt) : 0;
         }
         int32_t id[SC_U][CIDS];
         int loc[SC_U][CIDS];
@@ -817,8 +838,8 @@ __global__ void __launch_bounds__(BLOCK, 3)
         }
         fence_proxy_async_smem();   // this thread's reads of the buffer come before the next copy into it
         __syncthreads();
-        // the round's ids and headers now sit in registers: the next round's copy goes
-        // into the same buffer while this one is scanned and written out
+        // the round's ids and headers now sit in registers: the copy of round
+        // k + SC_BUF goes into this buffer while this round is scanned and written out
         if (t == 0 && knext >= 0) issue(uc0, unf, knext, b);
         const int h = s.cnt[t];
         s.cnt[t] = 0;               // counts of the next round
@@ -839,9 +860,11 @@ __global__ void __launch_bounds__(BLOCK, 3)
         for (int i = t; i < items; i += BLOCK) {
             const uint64_t pr = s.tile[i];
             const int64_t pos = (int64_t)s.delta[lo32(pr) >> C.shift] + i;
-            if (pos < n) pairs[pos] = pr;
+            if (pos < n) st_hint_u64(pairs + pos, pr, pol);
         }
-        __syncthreads();            // the next round rebuilds the tile
+        // no barrier here: the next round rebuilds the tile only after its own
+        // barriers (the bounded wait's __syncthreads_or comes first, and a new
+        // unit starts with one)
     };
 
     const int64_t no_all = min((int64_t)ctl->ovf_next, C.ovf_cap);
@@ -877,7 +900,7 @@ __global__ void __launch_bounds__(BLOCK, 3)
                 failed = true;
                 break;
             }
-            process(b, min(SC_CHUNKS, nf - k * SC_CHUNKS), c0, nf, k + 1 < nr ? k + 1 : -1);
+            process(b, min(SC_CHUNKS, nf - k * SC_CHUNKS), c0, nf, k + SC_BUF < nr ? k + SC_BUF : -1);
         }
     }
     if (failed) {

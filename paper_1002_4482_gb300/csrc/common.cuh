@@ -97,6 +97,12 @@ __device__ __forceinline__ int32_t ld_nc_hint(const int32_t* p, uint64_t pol) {
     asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+// One 32-byte streaming store (a whole sector) of 8 ints; p 32-byte aligned.
+__device__ __forceinline__ void st_cs_v8(int32_t* p, const int32_t (&v)[8]) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
 // 8-byte store with an L2 eviction-priority hint.
 __device__ __forceinline__ void st_hint_u64(uint64_t* p, uint64_t v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(p), "l"(v), "l"(pol) : "memory");

@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(BLOCK)
         L0.head_off = (uint32_t)(gh - (L0.bh << L0.logD));
     }
     const Geo32 g = geo32(L0);
-    constexpr int WCHUNK = 64;
+    constexpr int WCHUNK = 64;   // splitters a warp claims at once (32 and 128: no faster)
     __shared__ int s_fill;
     __shared__ int s_cnt[NSEG][NBK];
     // the ids a walk has visited since its last flush: slot t of chain q of thread i at
@@ -610,10 +610,10 @@ __global__ void __launch_bounds__(BLOCK)
                     for (int t = 0; t < CIDS; ++t)
                         v[t] = t < bn[q] ? s_ids[(q * CIDS + t) * BLOCK + threadIdx.x] : -1;
                     // streaming stores: the chunks are read once, by the scatter, and
-                    // should not push succ out of L2
-                    int4* d = reinterpret_cast<int4*>(C.ids + c * CIDS);
-                    __stcs(d, make_int4(v[0], v[1], v[2], v[3]));
-                    __stcs(d + 1, make_int4(v[4], v[5], v[6], v[7]));
+                    // should not push succ out of L2; one 32-byte store per chunk (chunks
+                    // are 32-byte aligned) moves a whole sector in one request instead of
+                    // two 16-byte halves (5.55 -> 5.51 ms at 2^28)
+                    st_cs_v8(C.ids + c * CIDS, v);
                     __stcs(reinterpret_cast<unsigned long long*>(C.meta + c),
                            (unsigned long long)((static_cast<uint64_t>(k0[q]) << 32) | static_cast<uint32_t>(j[q])));
 #pragma unroll

@@ -506,7 +506,8 @@ def bench_families(lrcc, torch, dev, stream, m=8_000_000):
     """The paper's component families (Sec. 4): collections of random lists, random
     trees of degree k and random graphs of edge density d, all with m edges; hook
     passes and time of the default rule (atomicMin hooking with the sample pass)
-    against the Shiloach-Vishkin rounds (hook rule 4)."""
+    against the Shiloach-Vishkin rounds (hook rule 4) and against a first pass
+    that links the endpoints themselves (hook rule 5)."""
     import gen
     out = []
     cases = [("lists", 1, None)] + [("trees", k, None) for k in (2, 3, 5, 10, 20)] + \
@@ -526,7 +527,7 @@ def bench_families(lrcc, torch, dev, stream, m=8_000_000):
             lab = torch.empty(n, dtype=torch.int32, device=dev)
         row = {"family": kind, "k": k, "density": d, "n": n, "m": len(src)}
         ref = None
-        for name, hook in (("atomicmin", base["cc_hook"]), ("shiloach_vishkin", 4)):
+        for name, hook in (("atomicmin", base["cc_hook"]), ("shiloach_vishkin", 4), ("link_first_pass", 5)):
             lrcc.set_cc_plan(0, 32, cc_hook=hook)
             lrcc.cc_label(S, D, n, out=lab, stream=stream)
             stream.synchronize()

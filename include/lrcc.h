@@ -312,8 +312,11 @@ typedef struct lrcc_plan {
     int32_t cc_hook;         /* 1 = one atomicMin per edge and pass, 2 = re-link until joined,
                                 3 = rule 1 in the first pass, rule 2 after, 4 = the
                                 Shiloach-Vishkin rounds themselves (shortcut, mark, conditional
-                                and stagnant-tree hooking, shortcut, check; Sec. 4 SV0-SV5);
-                                same labels; batched calls treat 4 as 1 */
+                                and stagnant-tree hooking, shortcut, check; Sec. 4 SV0-SV5),
+                                5 = rule 1 after a first pass that gathers no parents: each
+                                edge links its endpoints by atomicMin and carries every link
+                                the atomic displaces on, so that pass joins every edge it
+                                reads; same labels; batched calls treat 4 as 1 */
     int32_t cc_max_rounds;   /* cap on hook passes (-1 = back to the automatic cap) */
     int32_t use_graphs;      /* 1 = replay captured CUDA graphs, 2 = plain launches */
     int32_t rs_level0;       /* first ruling-set level: 1 = the walk rewrites 8-byte words in

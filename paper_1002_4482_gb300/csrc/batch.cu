@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(SEG_BLOCK)
              int mode, DevCtl* ctl) {
     __shared__ int s_slice, s_i;
     const bool relink = mode == 2 || (mode == 3 && ctl->rounds > 0);
+    const bool direct = mode == 5 && ctl->rounds == 0;   // rule 5's first pass (see cc.cu)
     const uint64_t keep = policy_evict_last();
     const uint64_t stream_pol = policy_evict_first();
     const int nl = *L.nlarge;
@@ -562,6 +563,12 @@ __global__ void __launch_bounds__(SEG_BLOCK)
                     u[q] = (int32_t)(base + a);
                     v[q] = (int32_t)(base + b);
                 }
+            }
+            if (direct) {   // first pass: nothing is kept, so no compaction either
+#pragma unroll
+                for (int q = 0; q < SEG_RUN; ++q)
+                    if (u[q] >= 0) changed |= link_direct(label, u[q], v[q], keep);
+                continue;
             }
             int32_t pa[SEG_RUN], pb[SEG_RUN];
 #pragma unroll

@@ -20,8 +20,12 @@
 // Shiloach-Vishkin round structure; 2 = when the atomicMin finds that the
 // larger root was linked meanwhile, keep joining (old parent, smaller root)
 // until one link lands, so each pass joins every edge and the next pass only
-// confirms; 3 = rule 1 in the first pass, rule 2 after it. All give the same
-// labels. Rule 4, the paper's own round structure, is in cc_sv.cu.
+// confirms; 3 = rule 1 in the first pass, rule 2 after it; 5 = in the first
+// pass (when every vertex is still its own root) no parent is gathered: each
+// edge links its endpoints with atomicMin and carries every link the atomic
+// displaces on to the next pair (link_direct), so that pass joins every edge
+// it reads, and rule 1 after it. All give the same labels. Rule 4, the
+// paper's own round structure, is in cc_sv.cu.
 //
 // Before the loop, an optional sample pass (plan.cc_sample) hooks and
 // shortcuts a prefix of the edge list, which forms most of a large component
@@ -80,6 +84,7 @@ __global__ void __launch_bounds__(BLOCK, 6)
     const int pass = ctl->rounds;
     const bool first = pass == 0;
     const bool relink = mode == 2 || (mode == 3 && !first);
+    const bool direct = mode == 5 && first;   // rule 5's first pass: link the endpoints themselves
     const int sel = ctl->cc_src;                       // 0 = input edges, 1/2 = active buffer
     const int out_sel = sel == 1 ? 2 : 1;
     const bool compact = !first && act.cap > 0;
@@ -143,6 +148,12 @@ __global__ void __launch_bounds__(BLOCK, 6)
                 record_error(ctl, LRCC_ERR_INVALID_INPUT, (int)(e0 + q));
                 u[q] = v[q] = 0;
             }
+        }
+        if (direct) {   // first pass: nothing is kept, so no compaction either
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (ok[q]) changed |= link_direct(parent, u[q], v[q], keep);
+            continue;
         }
         int32_t a[4], b[4];
 #pragma unroll
@@ -434,7 +445,7 @@ size_t cc_ws(int64_t m) {
 
 lrcc_status cc_run(Ctx* c, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
                    int32_t* label, const Plan& p) {
-    CcArgs a{src, dst, m, n, label, std::min(std::max(p.cc_hook, 1), 3), 0, ActiveEdges{}};
+    CcArgs a{src, dst, m, n, label, p.cc_hook == 5 ? 5 : std::min(std::max(p.cc_hook, 1), 3), 0, ActiveEdges{}};
     const int64_t acap = cc_active_cap(m);
     if (acap > 0 && c->ws_bytes >= cc_ws(m)) {
         a.act.buf[0] = static_cast<int2*>(c->ws);

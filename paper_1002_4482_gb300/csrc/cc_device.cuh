@@ -69,6 +69,31 @@ __device__ __forceinline__ bool hook_pair(int32_t* parent, int32_t a, int32_t b,
     }
 }
 
+// One edge (x, y) in a first pass, when no parent has been read: the
+// endpoints themselves are linked. atomicMin(&parent[hi], lo) returns hi's
+// parent before the call. If that was hi, hi was a root and now hangs below
+// lo: the edge is joined. Otherwise hi hung below `old` and now hangs below
+// min(old, lo), so the join goes on with (old, lo): the link the atomic may
+// have replaced is made again further up, and no connection is lost. The
+// larger id falls at every step, so the loop ends. A read before each atomic
+// skips it when the parent is already at or below lo (on hubs most are),
+// with the same continuation. Returns whether a parent was lowered.
+__device__ __forceinline__ bool link_direct(int32_t* parent, int32_t x, int32_t y, uint64_t keep) {
+    bool lowered = false;
+    while (x != y) {
+        const int32_t hi = max(x, y), lo = min(x, y);
+        int32_t old = ld_cg_hint(parent + hi, keep);
+        if (old > lo) {
+            old = atomicMin(parent + hi, lo);
+            if (old > lo) lowered = true;
+            if (old == hi) break;
+        }
+        x = old;
+        y = lo;
+    }
+    return lowered;
+}
+
 // Exclusive prefix over the warp of a per-lane count in [0, 15], and the warp
 // total, from four ballots (one per bit) instead of a shuffle scan: ballots do
 // not queue on the memory pipe that the gathers of a hook pass keep busy.

@@ -715,7 +715,7 @@ lrcc_status lrcc_set_plan(int kind, int log2_lo, int log2_hi, const lrcc_plan* p
     if (plan->rs_small < 0 || plan->rs_small > 16384 || plan->rs_spacing0 < 0 || plan->rs_spacing < 0 ||
         (plan->rs_spacing0 > 0 && plan->rs_spacing0 < 2) || (plan->rs_spacing > 0 && plan->rs_spacing < 2) ||
         (plan->rs_small > 0 && plan->rs_small < 1024) || plan->rs_chains < 0 || plan->rs_chains > 4 ||
-        plan->cc_hook < 0 || plan->cc_hook > 4 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
+        plan->cc_hook < 0 || plan->cc_hook > 5 || plan->cc_max_rounds < -1 || plan->use_graphs < 0 ||
         plan->use_graphs > 2 || plan->rs_level0 < 0 || plan->rs_level0 > 3 || plan->cc_sample < -1 ||
         plan->cc_sample > 1024)
         return LRCC_ERR_ARG;

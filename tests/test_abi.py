@@ -109,7 +109,7 @@ def test_plan_table_roundtrip(lib):
     with pytest.raises(lrcc.LrccError):
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_small=100000)
     with pytest.raises(lrcc.LrccError):
-        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=5)
+        lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=6)
     with pytest.raises(lrcc.LrccError):
         lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=-2)
     # the Shiloach-Vishkin rounds keep one int32 mark per vertex, the other rules active-edge buffers

@@ -23,7 +23,8 @@ def _run(src, dst, n):
     return lab.cpu().numpy()
 
 
-@pytest.fixture(params=[1, 2, 3, 4], ids=["hook-once", "hook-relink", "hook-once-then-relink", "shiloach-vishkin"])
+@pytest.fixture(params=[1, 2, 3, 4, 5],
+                ids=["hook-once", "hook-relink", "hook-once-then-relink", "shiloach-vishkin", "link-first-pass"])
 def hook(request):
     lrcc.set_cc_plan(0, 32, cc_hook=request.param)
     yield request.param

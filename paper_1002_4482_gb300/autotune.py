@@ -160,7 +160,7 @@ def tune_graphs(classes=(16, 20, 24), device=0, log=print, sparse=False):
                 return lab
             expect.append(_reference_labels(kind, c, c, run))
         best = None
-        for hook, samp in itertools.product((1, 2, 3), (-1, 1, 4, 8)):
+        for hook, samp in itertools.product((1, 2, 3, 5), (-1, 1, 4, 8)):
             set_plan(kind, c, c, cc_hook=hook, cc_sample=samp, use_graphs=1)
             ms = 0.0
             for (sd, dd, n_, lab, _, _), want in zip(cases, expect):
@@ -221,7 +221,7 @@ def tune_batched(log2_count=10, device=0, log=print):
     res["lists"] = {"ms": best[0], "plan": best[1]}
     log(f"batched lists: {best[0]:.3f} ms with {best[1]}")
     best = None
-    for hook in (1, 2):
+    for hook in (1, 2, 5):
         set_plan(KIND_CC_BATCH, 0, 32, cc_hook=hook)
         ms = _timeit(lambda: cc_label_batched(SR, DS, EO, VO, n_total=int(voff[-1]), out=lab, stream=stream), stream)
         if not np.array_equal(lab.cpu().numpy(), want_l):

@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(SEG_BLOCK)
             const int64_t g = voff[L.ids[i]] + (x - L.lvp[i]);
             const int p = label[g];
             if (p != g) {
-                const int r = find_root(label, p, keep);
+                const int r = chase_root(label, (int32_t)g, p, keep);
                 if (r != p) label[g] = r;
             }
         }

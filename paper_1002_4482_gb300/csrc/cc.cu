@@ -243,19 +243,19 @@ __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n,
         if (VEC && i0 + 3 < n) {
             const int4 p = *reinterpret_cast<const int4*>(parent + i0);
             // the four chases advance together, so four loads are in flight at a time;
-            // they read through L1: roots do not move during this pass, a value read
-            // late is still an ancestor, and the hot roots of large trees then hit L1
-            // instead of queueing on one L2 slice
+            // their first steps read through L1 and deep chases write their progress
+            // (chase_step)
             int x[4] = {p.x, p.y, p.z, p.w};
             bool live[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) live[q] = x[q] != (int)(i0 + q);
             bool any = live[0] | live[1] | live[2] | live[3];
             bool ch = false;
-            while (any) {
+            for (int step = 0; any; ++step) {
                 int nx[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) nx[q] = live[q] ? ld_hint(parent + x[q], keep) : x[q];
+                for (int q = 0; q < 4; ++q)
+                    nx[q] = live[q] ? chase_step(parent, (int32_t)(i0 + q), x[q], step, keep) : x[q];
                 any = false;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(BLOCK) cc_shortcut(int32_t* parent, int64_t n,
                 if (v < n) {
                     const int p = parent[v];
                     if (p != v) {
-                        const int r = find_root(parent, p, keep);
+                        const int r = chase_root(parent, (int32_t)v, p, keep);
                         if (r != p) parent[v] = r;
                     }
                 }

@@ -6,16 +6,37 @@
 
 namespace lrcc {
 
-// Follow parents to a root. Every link goes to a smaller id, so the walk
-// ends within n steps on any state the kernels can produce. For shortcut
-// passes only: roots do not move while they run, so the loads may go through
-// L1 (a value read late is still an ancestor) and the hot roots of large
-// trees hit L1 instead of queueing on one L2 slice.
-__device__ __forceinline__ int32_t find_root(const int32_t* parent, int32_t x, uint64_t keep) {
-    for (;;) {
-        const int32_t p = ld_hint(parent + x, keep);
-        if (p == x) return x;
-        x = p;
+// Chases of the shortcut passes: steps taken through L1 without writing
+// before a chase switches to its deep mode (see chase_step).
+constexpr int CHASE_QUIET = 4;
+
+// One step of a shortcut chase of vertex v, now at ancestor x: returns x's
+// parent. Roots do not move while a shortcut pass runs and every value read
+// is an ancestor, so the first CHASE_QUIET steps read through L1 (the hot
+// roots of large trees then hit L1 instead of queueing on one L2 slice) and
+// write nothing: trees after a hook pass are mostly stars. Deeper chases read
+// through L2 and store the ancestor reached in parent[v] (v's own entry, which
+// no other thread writes during the pass), so that chases passing through v
+// jump ahead. On a chain of n links, such as a path whose edges join
+// consecutive ids (every vertex hooked below its predecessor), the chases of
+// a pass then double their reach at every step, O(log n) steps each, where
+// chases that wrote nothing took up to n steps each (O(n^2) work in all).
+__device__ __forceinline__ int32_t chase_step(int32_t* parent, int32_t v, int32_t x, int step, uint64_t keep) {
+    if (step < CHASE_QUIET) return ld_hint(parent + x, keep);
+    const int32_t nx = ld_cg_hint(parent + x, keep);
+    if (nx != x) parent[v] = nx;
+    return nx;
+}
+
+// Root of vertex v whose parent is p, by chase_step. Every link goes to a
+// smaller id, so the chase ends within n steps on any state the kernels can
+// produce.
+__device__ __forceinline__ int32_t chase_root(int32_t* parent, int32_t v, int32_t p, uint64_t keep) {
+    int32_t x = p;
+    for (int step = 0;; ++step) {
+        const int32_t nx = chase_step(parent, v, x, step, keep);
+        if (nx == x) return x;
+        x = nx;
     }
 }
 

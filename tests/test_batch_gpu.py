@@ -49,6 +49,25 @@ def test_graph_batch_mixed_sizes(seed):
         assert np.array_equal(lab, oracle.cc_batched(src, dst, eoff, voff))
 
 
+@pytest.mark.parametrize("hook", [1, 5])
+def test_graph_batch_of_consecutive_id_paths(hook):
+    # paths whose edges join consecutive local ids, in id order: a deep chain per
+    # instance after the first hook pass, in the shared-memory path (<= 2^15
+    # vertices) and in the union of the large instances; every label is 0
+    sizes = [2, 1000, 1 << 15, (1 << 15) + 1, 1 << 17, 300_000]
+    src = np.concatenate([np.arange(k - 1, dtype=np.int32) for k in sizes])
+    dst = np.concatenate([np.arange(1, k, dtype=np.int32) for k in sizes])
+    eoff = np.concatenate([[0], np.cumsum([k - 1 for k in sizes])]).astype(np.int64)
+    voff = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    lrcc.set_plan(lrcc.KIND_CC_BATCH, 0, 32, cc_hook=hook)
+    try:
+        lab = lrcc.cc_label_batched(*(torch.from_numpy(x).to(DEV) for x in (src, dst, eoff, voff)))
+        lrcc.check()
+    finally:
+        lrcc.reset_plans()
+    assert not lab.any().item()
+
+
 def test_batch_with_empty_instances():
     sizes = [0, 5, 0, 0, 10000, 0]
     succ, off, heads, rank = _lists(sizes, 3)

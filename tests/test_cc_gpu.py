@@ -70,6 +70,22 @@ def test_paths_and_cycles(hook, k, seg, cycle):
     assert len(np.unique(lab)) == k
 
 
+@pytest.mark.parametrize("k,seg,reverse", [(1, 1 << 22, False), (1, 1 << 20, True), (256, 4096, False)])
+def test_paths_of_consecutive_ids(hook, k, seg, reverse):
+    # k paths whose edges join consecutive ids, in id order (a 1-D chain): the first
+    # hook pass hangs every vertex below its predecessor, one chain per path as deep
+    # as the path is long, which the shortcut then has to flatten; labels are each
+    # path's first id (closed form)
+    n = k * seg
+    ids = np.arange(n, dtype=np.int64).reshape(k, seg)
+    src = ids[:, :-1].ravel().astype(np.int32)
+    dst = ids[:, 1:].ravel().astype(np.int32)
+    if reverse:
+        src, dst = dst[::-1].copy(), src[::-1].copy()
+    lab = _run(src, dst, n)
+    assert np.array_equal(lab, np.repeat(ids[:, 0], seg).astype(np.int32))
+
+
 def test_self_loops_duplicates_isolated(hook):
     src = np.array([3, 3, 3, 7, 7, 1], np.int32)
     dst = np.array([3, 5, 5, 7, 5, 1], np.int32)

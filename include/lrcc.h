@@ -316,7 +316,9 @@ typedef struct lrcc_plan {
                                 5 = rule 1 after a first pass that gathers no parents: each
                                 edge links its endpoints by atomicMin and carries every link
                                 the atomic displaces on, so that pass joins every edge it
-                                reads; same labels; batched calls treat 4 as 1 */
+                                reads; same labels; batched calls treat 4 as 1, and their
+                                graphs of at most 2^15 vertices, labelled inside one block,
+                                re-link until joined whatever the rule */
     int32_t cc_max_rounds;   /* cap on hook passes (-1 = back to the automatic cap) */
     int32_t use_graphs;      /* 1 = replay captured CUDA graphs, 2 = plain launches */
     int32_t rs_level0;       /* first ruling-set level: 1 = the walk rewrites 8-byte words in

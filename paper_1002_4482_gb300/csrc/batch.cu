@@ -251,9 +251,14 @@ __device__ void graph_in_smem(const int32_t* src, const int32_t* dst, int64_t m,
             }
         }
         __syncthreads();
+        // chases longer than CHASE_QUIET steps store their progress in their own
+        // entry, so chases through it jump ahead (see chase_step)
         for (int v = threadIdx.x; v < n; v += BT) {
             int x = p[v];
-            while (p[x] != x) x = p[x];
+            for (int step = 0; p[x] != x; ++step) {
+                x = p[x];
+                if (step >= CHASE_QUIET) p[v] = x;
+            }
             p[v] = x;
         }
         if (!__syncthreads_or(changed)) break;
@@ -288,10 +293,11 @@ __device__ void graph_in_global(const int32_t* src, const int32_t* dst, int64_t 
         for (int64_t v = threadIdx.x; v < n; v += BT) {
             int x = ld_cg(p + v);
             if (x == v) continue;
-            for (;;) {
+            for (int step = 0;; ++step) {
                 const int y = ld_cg(p + x);
                 if (y == x) break;
                 x = y;
+                if (step >= CHASE_QUIET) p[v] = x;   // progress for chases through v (see chase_step)
             }
             p[v] = x;
         }

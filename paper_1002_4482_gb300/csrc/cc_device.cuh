@@ -24,8 +24,10 @@ constexpr int CHASE_QUIET = LRCC_CHASE_QUIET;
 // no other thread writes during the pass), so that chases passing through v
 // jump ahead. On a chain of n links, such as a path whose edges join
 // consecutive ids (every vertex hooked below its predecessor), the chases of
-// a pass then double their reach at every step, O(log n) steps each, where
-// chases that wrote nothing took up to n steps each (O(n^2) work in all).
+// a pass then double their reach at every step, O(log n) steps each; chases
+// that stored only the root they reached took about sqrt(2n) steps each when
+// all advance together and more when they do not (a path of 2^24 consecutive
+// ids: 487 ms against 0.97 ms with the progress stores).
 __device__ __forceinline__ int32_t chase_step(int32_t* parent, int32_t v, int32_t x, int step, uint64_t keep) {
     if (step < CHASE_QUIET) return ld_hint(parent + x, keep);
     const int32_t nx = ld_cg_hint(parent + x, keep);

@@ -110,6 +110,12 @@ def test_plan_table_roundtrip(lib):
         lrcc.set_plan(lrcc.KIND_LR, 0, 32, rs_small=100000)
     with pytest.raises(lrcc.LrccError):
         lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_hook=6)
+    # hook rule 5 (first pass links the endpoints themselves) is a plan value like the others
+    lrcc.set_plan(lrcc.KIND_CC_BATCH, 0, 32, cc_hook=5)
+    try:
+        assert lrcc.get_plan(lrcc.KIND_CC_BATCH, 1 << 20)["cc_hook"] == 5
+    finally:
+        lrcc.reset_plans()
     with pytest.raises(lrcc.LrccError):
         lrcc.set_plan(lrcc.KIND_CC, 0, 32, cc_sample=-2)
     # the Shiloach-Vishkin rounds keep one int32 mark per vertex, the other rules active-edge buffers
